@@ -1,0 +1,178 @@
+/*
+ * swgb300 — exact Smith-Waterman protein database search on one GB300 GPU.
+ *
+ * C ABI of the library (libswgb300.so). Every entry point scores protein
+ * queries against a protein database with recurrence (1) of Section II.A of
+ * Liu & Schmidt, "SWAPHI: Smith-Waterman Protein Database Search on Xeon Phi
+ * Coprocessors" (arXiv:1404.4152):
+ *
+ *   H[i][j] = max{ 0, H[i-1][j-1] + fsbt(S1[i], S2[j]), E[i][j], F[i][j] }
+ *   E[i][j] = max{ E[i-1][j] - alpha, H[i-1][j] - beta }
+ *   F[i][j] = max{ F[i][j-1] - alpha, H[i][j-1] - beta }
+ *
+ * with H = E = F = 0 on the borders; the score of a pair is the largest H.
+ * S1 is the query (rows) and S2 a database sequence (columns); fsbt(a, b) =
+ * matrix[a * alphabet + b], row = query residue. alpha is the gap extension
+ * penalty and beta the sum of the gap open and extension penalties, exactly as
+ * the recurrence uses them. Every score is exact (bit-identical to scalar int32
+ * arithmetic); no result is approximated.
+ *
+ * A search returns every score (database order) and the top_k hits ordered by
+ * score descending, equal scores by ascending database index (stage (iv) of
+ * the workflow in Section III).
+ *
+ * Conventions for every call:
+ *  - Status codes: SW_OK or an error; on error nothing is written to any
+ *    output and sw_last_error() returns a message for the calling thread.
+ *  - Pointers marked HOST are ordinary host memory (pageable or pinned);
+ *    pointers marked DEVICE are CUDA device memory on the database's device.
+ *    The caller owns every buffer it passes; the library copies what it needs
+ *    before returning (or, for the _device calls, before the work it enqueued
+ *    on the caller's stream completes).
+ *  - Residue codes are 0 .. alphabet-1, alphabet <= 32 (Section III.B.2:
+ *    |Sigma| < 32 for biological sequences). Scoring-matrix entries are int8.
+ *  - 0 <= alpha, beta <= 32767; top_k <= SW_MAX_TOP_K; a query has >= 1
+ *    residue; database sequences may be empty (score 0).
+ *  - Threads: a database handle may be searched from one thread at a time;
+ *    different handles are independent. A server handle is thread-safe.
+ *  - No exception crosses this interface.
+ */
+#ifndef SWGB300_SW_H
+#define SWGB300_SW_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SW_MAX_ALPHABET 32u
+#define SW_MAX_TOP_K 1024u
+
+typedef enum {
+    SW_OK = 0,
+    SW_ERR_INVALID_ARG = 1, /* a bad pointer, size, code, penalty or option */
+    SW_ERR_OOM = 2,         /* device or host memory (or the configured budget) exhausted */
+    SW_ERR_CUDA = 3,        /* a CUDA runtime call failed */
+    SW_ERR_TIMEOUT = 4,     /* a bounded wait ran out */
+    SW_ERR_BUSY = 5,        /* the server queue is full or the ticket is unknown */
+    SW_ERR_INTERNAL = 6     /* a broken internal invariant */
+} sw_status;
+
+/* Options for sw_db_load. Zero-initialise and set what you need; zero fields take defaults. */
+typedef struct {
+    int device;                 /* CUDA device ordinal (default 0) */
+    uint32_t long_threshold;    /* sequences longer than this go to the warp-per-pair kernel
+                                   (default 3000) */
+    uint64_t device_budget;     /* cap on the bytes this handle may allocate on the device
+                                   (0 = no cap); exceeding it gives SW_ERR_OOM */
+    uint32_t flags;             /* SW_DB_FLAG_* */
+} sw_db_opts;
+
+#define SW_DB_FLAG_FORCE_INT32 1u   /* skip the packed 16-bit kernels; everything in int32 */
+
+typedef struct sw_db sw_db;
+
+typedef struct {
+    uint64_t n_seqs;
+    uint64_t total_residues;     /* sum of database sequence lengths */
+    uint64_t device_bytes;       /* bytes this handle holds on the device */
+    uint32_t alphabet;
+    uint32_t max_length;
+    uint64_t n_long;             /* sequences above long_threshold */
+    int device;
+} sw_db_info;
+
+/* Per-call statistics (optional output of the search calls). */
+typedef struct {
+    uint64_t cells;              /* sum over pairs of |query| * |db sequence| (real residues) */
+    uint64_t recomputed;         /* sequences rescored in int32 after the 16-bit lanes saturated */
+    double kernel_ms;            /* device time from the first to the last kernel of the call */
+    double total_ms;             /* wall time of the whole call, copies included */
+} sw_stats;
+
+/*
+ * Load a database onto the device (stage (i)/(ii) set-up of Section III: the
+ * subject sequences are ordered by length, as the paper's offline index does,
+ * and laid out for the kernels).
+ *
+ *   residues : HOST, uint8 codes of all sequences concatenated (offsets[n_seqs] bytes)
+ *   offsets  : HOST, n_seqs + 1 ascending byte offsets; sequence s is
+ *              residues[offsets[s] .. offsets[s+1])
+ *   n_seqs   : number of sequences (>= 1)
+ *   alphabet : number of residue codes (1 .. 32); every code must be < alphabet
+ *   opts     : HOST, may be NULL (defaults)
+ *   out      : receives the handle; free it with sw_db_free
+ *
+ * Errors: SW_ERR_INVALID_ARG (bad code, offsets not ascending, ...), SW_ERR_OOM,
+ * SW_ERR_CUDA. The host arrays may be freed as soon as the call returns.
+ */
+sw_status sw_db_load(const uint8_t* residues, const uint64_t* offsets, uint64_t n_seqs,
+                     uint32_t alphabet, const sw_db_opts* opts, sw_db** out);
+
+/* Release a database and all its device memory. NULL is ignored. */
+void sw_db_free(sw_db* db);
+
+/* Describe a loaded database. */
+sw_status sw_db_get_info(const sw_db* db, sw_db_info* info);
+
+/*
+ * Search one query (HOST buffers; copies in and out are part of the call).
+ *
+ *   query      : HOST, qlen residue codes (< alphabet)
+ *   matrix     : HOST, alphabet * alphabet int8 scores, row = query residue
+ *   alpha,beta : gap extension / open-plus-extension penalties of recurrence (1)
+ *   top_k      : number of hits wanted (0 .. SW_MAX_TOP_K)
+ *   scores     : HOST, n_seqs int32, database order; may be NULL
+ *   top_scores : HOST, top_k int32; may be NULL when top_k == 0
+ *   top_index  : HOST, top_k uint64 database indices
+ *   n_top      : HOST, receives min(top_k, n_seqs)
+ *   stats      : HOST, may be NULL
+ */
+sw_status sw_search(sw_db* db, const uint8_t* query, uint32_t qlen, const int8_t* matrix,
+                    int32_t alpha, int32_t beta, uint32_t top_k, int32_t* scores,
+                    int32_t* top_scores, uint64_t* top_index, uint32_t* n_top, sw_stats* stats);
+
+/*
+ * Search one query with DEVICE buffers, enqueued on a caller stream
+ * (cudaStream_t passed as void*; NULL = the legacy default stream). The call
+ * returns after enqueueing; results are valid once the stream reaches them.
+ *
+ *   d_query      : DEVICE, qlen codes
+ *   d_matrix     : DEVICE, alphabet * alphabet int8
+ *   d_scores     : DEVICE, n_seqs int32 (database order); may be NULL
+ *   d_top_scores : DEVICE, top_k int32;  d_top_index : DEVICE, top_k uint64
+ *
+ * Codes in d_query are checked on the device: a code >= alphabet makes the
+ * result undefined but never an out-of-bounds access (it is clamped to the pad
+ * code, which scores 0). Use sw_search for validated input.
+ */
+sw_status sw_search_device(sw_db* db, const uint8_t* d_query, uint32_t qlen,
+                           const int8_t* d_matrix, int32_t alpha, int32_t beta, uint32_t top_k,
+                           int32_t* d_scores, int32_t* d_top_scores, uint64_t* d_top_index,
+                           void* stream);
+
+/*
+ * Search nq queries against the database in one batched launch sequence
+ * (HOST buffers). queries[q] has qlens[q] codes; scores may be NULL, else
+ * scores[q] is NULL or n_seqs int32. top_scores / top_index hold nq * top_k
+ * entries (row q = query q); n_top[q] receives min(top_k, n_seqs).
+ */
+sw_status sw_search_batch(sw_db* db, uint32_t nq, const uint8_t* const* queries,
+                          const uint32_t* qlens, const int8_t* matrix, int32_t alpha,
+                          int32_t beta, uint32_t top_k, int32_t* const* scores,
+                          int32_t* top_scores, uint64_t* top_index, uint32_t* n_top,
+                          sw_stats* stats);
+
+/* Message for the last non-OK status returned to this thread ("" if none). */
+const char* sw_last_error(void);
+
+/* Library version string. */
+const char* sw_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SWGB300_SW_H */
