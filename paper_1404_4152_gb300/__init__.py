@@ -1,0 +1,222 @@
+"""Python binding of libswgb300: exact Smith-Waterman protein database search on a GB300.
+
+Thin ctypes marshalling over the C ABI in ``include/sw.h``; every step of a
+search runs in the library's CUDA kernels. The functions carry the C names:
+
+    db = sw_db_load(residues, offsets, alphabet=20)
+    scores, top_scores, top_index, stats = sw_search(db, query, matrix, alpha, beta, top_k)
+    sw_search_device(db, d_query, d_matrix, alpha, beta, top_k, d_scores, d_top_s, d_top_i, stream)
+    sw_db_free(db)
+
+Scoring follows recurrence (1) of Section II.A of the SWAPHI paper: alpha is
+the gap extension penalty, beta the sum of the gap open and extension
+penalties, and matrix[a, b] scores query residue a against database residue b.
+
+There is no CPU fallback: importing the binding fails loudly if the compiled
+library is missing (run ``__graft_entry__.build()`` or ``python -m
+paper_1404_4152_gb300.build``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+SW_MAX_ALPHABET = 32
+SW_MAX_TOP_K = 1024
+SW_DB_FLAG_FORCE_INT32 = 1
+
+_STATUS = {0: "SW_OK", 1: "SW_ERR_INVALID_ARG", 2: "SW_ERR_OOM", 3: "SW_ERR_CUDA",
+           4: "SW_ERR_TIMEOUT", 5: "SW_ERR_BUSY", 6: "SW_ERR_INTERNAL"}
+
+
+class SwError(RuntimeError):
+    """A non-OK status from the library; ``status`` holds the code name."""
+
+    def __init__(self, code: int, message: str):
+        self.code = code
+        self.status = _STATUS.get(code, str(code))
+        super().__init__(f"{self.status}: {message}")
+
+
+class sw_db_opts(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("long_threshold", ctypes.c_uint32),
+                ("device_budget", ctypes.c_uint64), ("flags", ctypes.c_uint32)]
+
+
+class sw_db_info(ctypes.Structure):
+    _fields_ = [("n_seqs", ctypes.c_uint64), ("total_residues", ctypes.c_uint64),
+                ("device_bytes", ctypes.c_uint64), ("alphabet", ctypes.c_uint32),
+                ("max_length", ctypes.c_uint32), ("n_long", ctypes.c_uint64),
+                ("device", ctypes.c_int)]
+
+
+class sw_stats(ctypes.Structure):
+    _fields_ = [("cells", ctypes.c_uint64), ("recomputed", ctypes.c_uint64),
+                ("kernel_ms", ctypes.c_double), ("total_ms", ctypes.c_double)]
+
+
+# Every entry point the header declares: (name, restype, argtypes).
+_P, _U8, _U32, _U64, _I32 = (ctypes.c_void_p, ctypes.c_uint8, ctypes.c_uint32, ctypes.c_uint64,
+                             ctypes.c_int32)
+SIGNATURES = {
+    "sw_db_load": (ctypes.c_int, [_P, _P, _U64, _U32, _P, ctypes.POINTER(_P)]),
+    "sw_db_free": (None, [_P]),
+    "sw_db_get_info": (ctypes.c_int, [_P, _P]),
+    "sw_search": (ctypes.c_int, [_P, _P, _U32, _P, _I32, _I32, _U32, _P, _P, _P, _P, _P]),
+    "sw_search_device": (ctypes.c_int, [_P, _P, _U32, _P, _I32, _I32, _U32, _P, _P, _P, _P]),
+    "sw_search_batch": (ctypes.c_int, [_P, _U32, _P, _P, _P, _I32, _I32, _U32, _P, _P, _P, _P,
+                                       _P]),
+    "sw_last_error": (ctypes.c_char_p, []),
+    "sw_version": (ctypes.c_char_p, []),
+}
+
+_lib = None
+
+
+def load_library(path: str | None = None):
+    """Load libswgb300.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or _build.lib_path()
+    if not os.path.exists(p):
+        raise ImportError(f"libswgb300.so is not built ({p}); run __graft_entry__.build()")
+    lib = ctypes.CDLL(p)
+    for name, (res, args) in SIGNATURES.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def _check(code: int):
+    if code != 0:
+        raise SwError(code, load_library().sw_last_error().decode())
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data if a.size else None
+
+
+class Database:
+    """A database resident on the device (an ``sw_db*``)."""
+
+    def __init__(self, handle, n_seqs: int, alphabet: int):
+        self.handle = handle
+        self.n_seqs = n_seqs
+        self.alphabet = alphabet
+
+    def info(self) -> dict:
+        return sw_db_get_info(self)
+
+    def free(self):
+        if self.handle:
+            load_library().sw_db_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.free()
+
+
+def sw_db_load(residues, offsets, alphabet: int = 20, device: int = 0, long_threshold: int = 0,
+               device_budget: int = 0, flags: int = 0) -> Database:
+    """Load database sequences (uint8 codes, uint64 offsets of n+1 entries) onto the GPU."""
+    lib = load_library()
+    res = np.ascontiguousarray(residues, dtype=np.uint8)
+    off = np.ascontiguousarray(offsets, dtype=np.uint64)
+    opts = sw_db_opts(device, long_threshold, device_budget, flags)
+    h = ctypes.c_void_p()
+    _check(lib.sw_db_load(_ptr(res), _ptr(off), off.size - 1, alphabet, ctypes.byref(opts),
+                          ctypes.byref(h)))
+    return Database(h, off.size - 1, alphabet)
+
+
+def sw_db_free(db: Database):
+    db.free()
+
+
+def sw_db_get_info(db: Database) -> dict:
+    info = sw_db_info()
+    _check(load_library().sw_db_get_info(db.handle, ctypes.byref(info)))
+    return {k: getattr(info, k) for k, _ in sw_db_info._fields_}
+
+
+def sw_search(db: Database, query, matrix, alpha: int, beta: int, top_k: int = 10,
+              want_scores: bool = True):
+    """One query, host buffers -> (scores int32 | None, top_scores, top_index, stats dict)."""
+    q = np.ascontiguousarray(query, dtype=np.uint8)
+    m = np.ascontiguousarray(matrix, dtype=np.int8)
+    scores = np.empty(db.n_seqs, dtype=np.int32) if want_scores else None
+    ts = np.empty(max(top_k, 1), dtype=np.int32)
+    ti = np.empty(max(top_k, 1), dtype=np.uint64)
+    n_top = ctypes.c_uint32(0)
+    st = sw_stats()
+    _check(load_library().sw_search(db.handle, _ptr(q), q.size, _ptr(m), int(alpha), int(beta),
+                                    int(top_k), _ptr(scores) if scores is not None else None,
+                                    _ptr(ts), _ptr(ti), ctypes.byref(n_top), ctypes.byref(st)))
+    k = n_top.value
+    return scores, ts[:k].copy(), ti[:k].copy(), {f: getattr(st, f) for f, _ in sw_stats._fields_}
+
+
+def sw_search_device(db: Database, d_query, qlen: int, d_matrix, alpha: int, beta: int,
+                     top_k: int, d_scores, d_top_scores, d_top_index, stream=None):
+    """One query on DEVICE buffers (torch tensors or raw pointers), enqueued on ``stream``."""
+
+    def addr(x):
+        if x is None:
+            return None
+        if isinstance(x, int):
+            return x
+        return x.data_ptr()
+
+    s = stream
+    if s is not None and not isinstance(s, int):
+        s = s.cuda_stream
+    _check(load_library().sw_search_device(db.handle, addr(d_query), int(qlen), addr(d_matrix),
+                                           int(alpha), int(beta), int(top_k), addr(d_scores),
+                                           addr(d_top_scores), addr(d_top_index), s))
+
+
+def sw_search_batch(db: Database, queries, matrix, alpha: int, beta: int, top_k: int = 10,
+                    want_scores: bool = False):
+    """Several queries -> (list of score arrays | None, top_scores [nq,k], top_index [nq,k],
+    n_top [nq], stats dict)."""
+    qs = [np.ascontiguousarray(q, dtype=np.uint8) for q in queries]
+    nq = len(qs)
+    m = np.ascontiguousarray(matrix, dtype=np.int8)
+    qptr = (ctypes.c_void_p * nq)(*[q.ctypes.data for q in qs])
+    qlen = np.array([q.size for q in qs], dtype=np.uint32)
+    score_rows = [np.empty(db.n_seqs, dtype=np.int32) for _ in qs] if want_scores else None
+    sptr = (ctypes.c_void_p * nq)(*[s.ctypes.data for s in score_rows]) if want_scores else None
+    ts = np.zeros((nq, max(top_k, 1)), dtype=np.int32)
+    ti = np.zeros((nq, max(top_k, 1)), dtype=np.uint64)
+    nt = np.zeros(nq, dtype=np.uint32)
+    st = sw_stats()
+    _check(load_library().sw_search_batch(db.handle, nq, qptr, _ptr(qlen), _ptr(m), int(alpha),
+                                          int(beta), int(top_k), sptr, _ptr(ts), _ptr(ti),
+                                          _ptr(nt), ctypes.byref(st)))
+    return (score_rows, ts[:, :top_k], ti[:, :top_k], nt,
+            {f: getattr(st, f) for f, _ in sw_stats._fields_})
+
+
+def sw_last_error() -> str:
+    return load_library().sw_last_error().decode()
+
+
+def sw_version() -> str:
+    return load_library().sw_version().decode()

@@ -1,0 +1,80 @@
+// The database handle and the host-side search plumbing shared by the
+// library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <utility>
+#include <vector>
+
+#include "sw.h"
+#include "sw_internal.h"
+
+struct sw_db {
+    // identity
+    int device = 0;
+    uint32_t alphabet = 0;
+    uint64_t n_seqs = 0;
+    uint64_t total_residues = 0;
+    uint32_t max_len = 0;
+    uint32_t long_threshold = 3000;
+    uint64_t budget = 0;
+    uint64_t dev_bytes = 0;
+    uint32_t flags = 0;
+    int nsm = 0;
+
+    cudaStream_t stream = nullptr;       // the library's own stream (host-buffer calls)
+    cudaStream_t stream_long = nullptr;  // side stream for the long-sequence kernel
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_t0 = nullptr, ev_t1 = nullptr;
+
+    // length-sorted tiles (descending length); tiles [0, n_long_tiles) hold the
+    // sequences above long_threshold
+    uint64_t n_long = 0, n_tiles = 0, n_long_tiles = 0, tile_bytes = 0;
+    uint32_t max_len_long = 0, max_len_short = 0;
+    std::vector<uint32_t> tile_len_host;
+    uint8_t* d_tile_data = nullptr;
+    uint64_t* d_tile_off = nullptr;
+    uint32_t* d_tile_len = nullptr;
+    uint32_t* d_sorted = nullptr;  // sorted position -> original index
+    int32_t* d_scores = nullptr;   // internal score row (original order)
+    uint32_t* d_flags = nullptr;   // sorted positions rescored in int32
+    uint32_t* d_misc = nullptr;
+
+    // search scratch
+    uint32_t* d_counters = nullptr;  // 0: short work, 1: long work, 2: rescoring work, 3: flags
+    uint2* d_bnd_short = nullptr;
+    uint64_t bstride_short = 0;
+    int grid_short = 0;
+    uint2* d_bnd_long = nullptr;
+    uint64_t bstride_long = 0;
+    int grid_long = 0;
+    uint2* d_bnd_rescore = nullptr;
+    uint64_t bstride_rescore = 0;
+    int grid_rescore = 0;
+    void* d_topk = nullptr;
+    swgb::TopkScratch topk{};
+    uint32_t topk_nq = 0;
+    uint8_t* d_query = nullptr;
+    uint32_t query_cap = 0;
+    int8_t* d_matrix = nullptr;
+    int32_t* d_top_scores = nullptr;
+    uint64_t* d_top_index = nullptr;
+    void* h_pinned = nullptr;
+
+    std::vector<std::pair<void*, size_t>> allocs;
+};
+
+namespace swgb {
+
+sw_status fail(sw_status st, const char* fmt, ...);
+sw_status cuda_fail(cudaError_t e, const char* what);
+void clear_error();
+cudaError_t db_malloc(sw_db* db, void** p, size_t bytes);
+void db_free(sw_db* db, void* p, size_t bytes);
+sw_status db_alloc(sw_db* db, void** p, size_t bytes, const char* what);
+
+}  // namespace swgb
+
+// Allocate the per-handle search scratch (boundary rows, counters, top-k).
+sw_status sw_db_prepare_search(sw_db* db);
