@@ -1,0 +1,379 @@
+#!/usr/bin/env python3
+"""Benchmark: exact Smith-Waterman protein database search on GB300, in GCUPS.
+
+Workload (default): 20 queries of 144..5,478 residues (geometrically spaced,
+the paper's query-length range) searched one at a time against 2,000,000
+synthetic database sequences (~700 M residues, log-normal lengths mean 350 /
+sd 250, Robinson-Robinson composition), BLOSUM62, beta = 11, alpha = 1, top 10.
+One step = all 20 searches (every DP cell of every pair, rescoring and top-k
+included). GCUPS = sum(|query|) * sum(|db sequence|) / seconds.
+
+  value      device-resident: queries, matrix and outputs in HBM, timed with
+             CUDA events on the stream the library launches on.
+  e2e        the same searches through the host-buffer call sw_search: query
+             copied in from pinned memory, every score and the top-k copied
+             back each call; wall-clock.
+  roofline   the dominant kernel (wavefront over the shorter sequences):
+             algorithmic ALU lane-operations / its mean launch time, against the
+             ALU-pipe peak at the SM clock sampled during the run.
+  cpu_baseline  the CPU oracle on a bounded sample of the same workload.
+
+--impl reference times the CPU oracle itself as the reference arm.
+Under torchrun each rank searches its own database shard (weak scaling); the
+JSON line reports the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+ALU_OPS_PER_CELL = 5          # max(E,F); add+max+0 for H; add+max for E; add+max for F; running max
+ALU_LANES_PER_CLK_SM = 64     # 32-bit lanes per clock per SM on the integer ALU pipe (4 x 16)
+S16X2_CELLS_PER_LANE = 2      # one 32-bit lane holds two 16-bit DP cells
+PAPER_PHI_GCUPS_MAX = 58.8    # SWAPHI InterSP, one Xeon Phi 5110P, TrEMBL (Section IV.A)
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--n-seqs", type=int, default=2_000_000)
+    p.add_argument("--n-queries", type=int, default=20)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=15.0)
+    return p.parse_args()
+
+
+def dist_info():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling in the background during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str | None):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                   "-lms", "200"]
+            if self.gpu_id:
+                cmd += ["-i", self.gpu_id]
+            self.proc = subprocess.Popen(cmd, stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), float(parts[3]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[3]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "power_w_max": max(r[2] for r in rows), "samples": len(rows), "reasons": reasons}
+
+
+def cpu_oracle_sample(w, seconds: float, threads: int):
+    """Time the oracle on all queries x the first S database sequences (~`seconds` of work)."""
+    import oracle
+
+    # calibrate on a small slice with a mid-length query
+    q0 = w.queries[len(w.queries) // 2]
+    n_cal = 300
+    t = time.perf_counter()
+    oracle.scores(q0, w.residues, w.offsets[: n_cal + 1], w.matrix, w.alpha, w.beta, nthreads=threads)
+    dt = time.perf_counter() - t
+    rate = q0.size * int(w.offsets[n_cal]) / max(dt, 1e-6)  # cells/s
+    qsum = sum(int(q.size) for q in w.queries)
+    per_seq = float(w.offsets[-1]) / w.n_seqs
+    S = int(max(64, min(w.n_seqs, seconds * rate / (qsum * per_seq))))
+    for _ in range(3):  # grow the sample until it takes about `seconds`
+        off = w.offsets[: S + 1]
+        t = time.perf_counter()
+        for q in w.queries:
+            oracle.scores(q, w.residues, off, w.matrix, w.alpha, w.beta, nthreads=threads)
+        dt = time.perf_counter() - t
+        if dt >= 0.6 * seconds or S >= w.n_seqs:
+            break
+        S = int(min(w.n_seqs, S * seconds / max(dt, 1e-3)))
+    cells = qsum * int(off[-1])
+    return cells / dt / 1e9, {"sequences": S, "residues": int(off[-1]), "cells": cells, "seconds": dt}
+
+
+def build_workload(args, rank):
+    return synth.config1(seed=1405 + 1000 * rank, n_seqs=args.n_seqs, n_queries=args.n_queries)
+
+
+def workload_config(w, args, world):
+    return {
+        "workload": (f"config1: {len(w.queries)} queries of {min(q.size for q in w.queries)}.."
+                     f"{max(q.size for q in w.queries)} aa, one at a time, vs {w.n_seqs:,} "
+                     f"sequences ({w.db_residues / 1e6:.0f} M aa) per GPU; BLOSUM62, beta={w.beta}, "
+                     f"alpha={w.alpha}; every score + top-{w.top_k}"),
+        "global_batch": len(w.queries) * world,
+        "db_sequences_per_gpu": w.n_seqs,
+        "db_residues_per_gpu": w.db_residues,
+        "query_lengths": [int(q.size) for q in w.queries],
+        "parallelism": f"db-shard x{world}" if world > 1 else "single GPU",
+        "l2": "inputs larger than L2 (database resident in HBM, ~0.7 GB per GPU > 129 MB L2)",
+    }
+
+
+def run_reference(args):
+    world, rank, _ = dist_info()
+    if rank != 0:
+        return 0
+    w = build_workload(args, 0)
+    threads = os.cpu_count() or 1
+    budget = max(2.0, min(12.0, 150.0 / max(1, args.steps + args.warmup)))
+    vals = []
+    info = None
+    for i in range(args.warmup + args.steps):
+        g, info = cpu_oracle_sample(w, budget, threads)
+        if i >= args.warmup:
+            vals.append(g)
+    v = statistics.median(vals) if vals else 0.0
+    line = {
+        "impl": "reference", "metric": "GCUPS", "value": v, "unit": "GCUPS", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": info["seconds"] * 1e3 if info else None, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": workload_config(w, args, 1),
+        "cpu_baseline": {"value": v, "unit": "GCUPS", "cores": threads, "kind": "oracle",
+                         "sample": f"all {len(w.queries)} queries x the first {info['sequences']} "
+                                   f"database sequences ({info['residues']} residues) per step"},
+        "e2e": {"value": v, "unit": "GCUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    world, rank, local = dist_info()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_1404_4152_gb300 import build as swbuild
+
+    swbuild.build()
+    import paper_1404_4152_gb300 as sw
+
+    w = build_workload(args, rank)
+    db = sw.sw_db_load(w.residues, w.offsets, alphabet=20, device=local, flags=sw.SW_DB_FLAG_PROFILE)
+    n = w.n_seqs
+    qlens = [int(q.size) for q in w.queries]
+    qoff = np.concatenate([[0], np.cumsum(qlens)]).astype(np.int64)
+    d_q = torch.from_numpy(np.concatenate(w.queries)).to(dev)
+    d_m = torch.from_numpy(w.matrix.copy()).to(dev)
+    d_s = torch.empty(n, dtype=torch.int32, device=dev)
+    k = w.top_k
+    d_ts = torch.empty((len(qlens), k), dtype=torch.int32, device=dev)
+    d_ti = torch.empty((len(qlens), k), dtype=torch.int64, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+
+    def step():
+        for i, L in enumerate(qlens):
+            sw.sw_search_device(db, d_q.data_ptr() + int(qoff[i]), L, d_m, w.alpha, w.beta, k, d_s,
+                                d_ts[i], d_ti[i], stream)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    for _ in range(args.warmup):
+        step()
+    stream.synchronize()
+    torch.cuda.synchronize()
+    barrier()
+
+    props = torch.cuda.get_device_properties(dev)
+    gpu_id = None
+    try:
+        gpu_id = "GPU-" + str(props.uuid)
+    except Exception:
+        gpu_id = None
+    sampler = ClockSampler(gpu_id)
+    sw.sw_db_reset_profile(db)
+    sampler.start()
+    time.sleep(0.4)
+    torch.cuda.synchronize()
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    stream.synchronize()
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    prof = sw.sw_db_get_profile(db)
+
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    ms_max = float(t.item())
+    cells_rank = sum(qlens) * w.db_residues * args.steps
+    cells_all = cells_rank * world
+    value = cells_all / (ms_max / 1e3) / 1e9
+
+    # per-query GCUPS (outside the timed region)
+    per_query = []
+    for i, L in enumerate(qlens):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sw.sw_search_device(db, d_q.data_ptr() + int(qoff[i]), L, d_m, w.alpha, w.beta, k, d_s,
+                            d_ts[i], d_ti[i], stream)
+        b.record(stream)
+        stream.synchronize()
+        per_query.append({"qlen": L, "gcups": L * w.db_residues / (a.elapsed_time(b) / 1e3) / 1e9})
+
+    # roofline of the dominant kernel
+    ph = prof["phases"]
+    dom = "wavefront"  # the search kernel: every DP cell of both length bins
+    d = ph[dom]
+    mean_ms = d["ms"] / max(1, d["calls"])
+    cells_per_launch = d["cells"] / max(1, d["calls"])
+    achieved = ALU_OPS_PER_CELL * cells_per_launch / (mean_ms / 1e3) / 1e9  # Gop/s
+    nsm = props.multi_processor_count
+    sm_mhz = clocks["sm_mhz"] if clocks else 2070.0
+    peak = nsm * sm_mhz * 1e6 * ALU_LANES_PER_CLK_SM * S16X2_CELLS_PER_LANE / 1e9
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tfile):
+        try:
+            tj = json.load(open(tfile))
+            if tj.get("kernel") == dom and tj.get("bytes_per_cell"):
+                traffic = tj["bytes_per_cell"] * cells_per_launch
+        except Exception:
+            traffic = None
+    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "Gop/s",
+                "frac": achieved / peak, "traffic": traffic,
+                "per_unit": f"{ALU_OPS_PER_CELL} integer ALU lane-ops per DP cell; "
+                            f"{cells_per_launch:.4g} cells per launch, mean launch {mean_ms:.2f} ms",
+                "peak_basis": f"{nsm} SMs x {sm_mhz:.0f} MHz (sampled) x {ALU_LANES_PER_CLK_SM} ALU "
+                              f"lanes/clk/SM x {S16X2_CELLS_PER_LANE} (s16x2)"}
+
+    # end to end through the host-buffer call
+    e2e = None
+    if not args.no_e2e:
+        pinned_q = [torch.from_numpy(q.copy()).pin_memory() for q in w.queries]
+        pinned_s = torch.empty(n, dtype=torch.int32).pin_memory()
+        import ctypes
+
+        lib = sw.load_library()
+        mat = np.ascontiguousarray(w.matrix, dtype=np.int8)
+        ts = np.empty(k, np.int32)
+        ti = np.empty(k, np.uint64)
+        ntop = ctypes.c_uint32()
+
+        def e2e_step():
+            for q in pinned_q:
+                rc = lib.sw_search(db.handle, q.data_ptr(), q.numel(), mat.ctypes.data, w.alpha,
+                                   w.beta, k, pinned_s.data_ptr(), ts.ctypes.data, ti.ctypes.data,
+                                   ctypes.byref(ntop), None)
+                if rc != 0:
+                    raise sw.SwError(rc, sw.sw_last_error())
+
+        e2e_step()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        t1 = time.perf_counter()
+        tt = torch.tensor([t1 - t0], dtype=torch.float64, device=dev)
+        if world > 1:
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        e2e = {"value": cells_all / float(tt.item()) / 1e9, "unit": "GCUPS",
+               "h2d_bytes_per_step": int(sum(qlens) + len(qlens) * w.matrix.size),
+               "d2h_bytes_per_step": int(len(qlens) * (4 * n + 12 * k + 4))}
+
+    cpu = None
+    if not args.no_cpu and world == 1 and rank == 0:
+        threads = os.cpu_count() or 1
+        g, info = cpu_oracle_sample(w, args.cpu_seconds, threads)
+        cpu = {"value": g, "unit": "GCUPS", "cores": threads, "kind": "oracle",
+               "sample": f"all {len(w.queries)} queries x the first {info['sequences']} database "
+                         f"sequences ({info['residues']} residues), {info['seconds']:.1f} s"}
+
+    line = {
+        "metric": "GCUPS", "value": value, "unit": "GCUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "s16x2", "data": "synthetic",
+        "config": workload_config(w, args, world),
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+        "gpu_launches": int(prof["launches"]),
+        "phases_ms": {p: ph[p]["ms"] for p in ph},
+        "per_query": per_query,
+        "context": {"paper_xeon_phi_gcups_max": PAPER_PHI_GCUPS_MAX},
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    db.free()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -71,6 +71,7 @@ typedef struct {
 } sw_db_opts;
 
 #define SW_DB_FLAG_FORCE_INT32 1u   /* skip the packed 16-bit kernels; everything in int32 */
+#define SW_DB_FLAG_PROFILE 2u       /* time every kernel phase with CUDA events (sw_db_get_profile) */
 
 typedef struct sw_db sw_db;
 
@@ -164,6 +165,26 @@ sw_status sw_search_batch(sw_db* db, uint32_t nq, const uint8_t* const* queries,
                           int32_t beta, uint32_t top_k, int32_t* const* scores,
                           int32_t* top_scores, uint64_t* top_index, uint32_t* n_top,
                           sw_stats* stats);
+
+/*
+ * Per-phase kernel timing of a handle loaded with SW_DB_FLAG_PROFILE (the
+ * tracing subsystem). Phases: 0 = the wavefront search kernel (both
+ * length bins), 1 = int32 rescoring, 2 = top-k, 3 = the batched search
+ * kernel. ms[p] is the summed device time of phase p measured
+ * with CUDA events on the stream it ran on, calls[p] the number of timed
+ * launches, cells[p] the DP cells it processed (sum of |query| * |sequence|
+ * over real residues). launches counts every kernel the handle enqueued since
+ * load or the last reset, timed or not. Reading waits for the timed work.
+ */
+typedef struct {
+    uint64_t launches;
+    uint64_t calls[4];
+    uint64_t cells[4];
+    double ms[4];
+} sw_profile;
+
+sw_status sw_db_get_profile(sw_db* db, sw_profile* out);
+sw_status sw_db_reset_profile(sw_db* db);
 
 /* Message for the last non-OK status returned to this thread ("" if none). */
 const char* sw_last_error(void);

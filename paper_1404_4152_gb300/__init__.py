@@ -28,6 +28,8 @@ from . import build as _build
 SW_MAX_ALPHABET = 32
 SW_MAX_TOP_K = 1024
 SW_DB_FLAG_FORCE_INT32 = 1
+SW_DB_FLAG_PROFILE = 2
+PHASES = ("wavefront", "rescore_int32", "topk", "batch")
 
 _STATUS = {0: "SW_OK", 1: "SW_ERR_INVALID_ARG", 2: "SW_ERR_OOM", 3: "SW_ERR_CUDA",
            4: "SW_ERR_TIMEOUT", 5: "SW_ERR_BUSY", 6: "SW_ERR_INTERNAL"}
@@ -59,6 +61,11 @@ class sw_stats(ctypes.Structure):
                 ("kernel_ms", ctypes.c_double), ("total_ms", ctypes.c_double)]
 
 
+class sw_profile(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_uint64), ("calls", ctypes.c_uint64 * 4),
+                ("cells", ctypes.c_uint64 * 4), ("ms", ctypes.c_double * 4)]
+
+
 # Every entry point the header declares: (name, restype, argtypes).
 _P, _U8, _U32, _U64, _I32 = (ctypes.c_void_p, ctypes.c_uint8, ctypes.c_uint32, ctypes.c_uint64,
                              ctypes.c_int32)
@@ -70,6 +77,8 @@ SIGNATURES = {
     "sw_search_device": (ctypes.c_int, [_P, _P, _U32, _P, _I32, _I32, _U32, _P, _P, _P, _P]),
     "sw_search_batch": (ctypes.c_int, [_P, _U32, _P, _P, _P, _I32, _I32, _U32, _P, _P, _P, _P,
                                        _P]),
+    "sw_db_get_profile": (ctypes.c_int, [_P, _P]),
+    "sw_db_reset_profile": (ctypes.c_int, [_P]),
     "sw_last_error": (ctypes.c_char_p, []),
     "sw_version": (ctypes.c_char_p, []),
 }
@@ -212,6 +221,19 @@ def sw_search_batch(db: Database, queries, matrix, alpha: int, beta: int, top_k:
                                           _ptr(nt), ctypes.byref(st)))
     return (score_rows, ts[:, :top_k], ti[:, :top_k], nt,
             {f: getattr(st, f) for f, _ in sw_stats._fields_})
+
+
+def sw_db_get_profile(db: Database) -> dict:
+    """Per-phase device time of a handle loaded with SW_DB_FLAG_PROFILE."""
+    p = sw_profile()
+    _check(load_library().sw_db_get_profile(db.handle, ctypes.byref(p)))
+    return {"launches": p.launches,
+            "phases": {name: {"calls": p.calls[i], "cells": p.cells[i], "ms": p.ms[i]}
+                       for i, name in enumerate(PHASES)}}
+
+
+def sw_db_reset_profile(db: Database):
+    _check(load_library().sw_db_reset_profile(db.handle))
 
 
 def sw_last_error() -> str:

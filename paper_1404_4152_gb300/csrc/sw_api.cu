@@ -114,6 +114,8 @@ void release(sw_db* db) {
     if (db->ev_t0) cudaEventDestroy(db->ev_t0);
     if (db->ev_t1) cudaEventDestroy(db->ev_t1);
     if (db->h_pinned) cudaFreeHost(db->h_pinned);
+    for (auto& t : db->pending) { cudaEventDestroy(t.a); cudaEventDestroy(t.b); }
+    for (auto ev : db->event_pool) cudaEventDestroy(ev);
     delete db;
 }
 
@@ -219,6 +221,13 @@ extern "C" sw_status sw_db_load(const uint8_t* residues, const uint64_t* offsets
     uint64_t n_long = 0;
     for (uint64_t s = 0; s < n_seqs; ++s) n_long += len[s] > db->long_threshold;
     db->n_long = n_long;
+    {
+        // residues per bin: the long bin is tiles [0, n_long_tiles)
+        const uint64_t long_positions = ((n_long + kTileSeqs - 1) / kTileSeqs) * kTileSeqs;
+        for (uint64_t p = 0; p < std::min<uint64_t>(long_positions, sorted.size()); ++p)
+            if (sorted[p] != 0xffffffffu) db->residues_long += len[sorted[p]];
+        db->residues_short = total - db->residues_long;
+    }
     db->n_tiles = n_tiles;
     db->n_long_tiles = (n_long + kTileSeqs - 1) / kTileSeqs;
     db->tile_bytes = off;

@@ -63,6 +63,22 @@ struct sw_db {
     void* h_pinned = nullptr;
 
     std::vector<std::pair<void*, size_t>> allocs;
+
+    // residues of the sequences in each bin (for cell counts)
+    uint64_t residues_short = 0, residues_long = 0;
+
+    // profiling (SW_DB_FLAG_PROFILE)
+    struct Timed {
+        int phase;
+        cudaEvent_t a, b;
+        uint64_t cells;
+    };
+    std::vector<Timed> pending;
+    std::vector<cudaEvent_t> event_pool;
+    uint64_t launches = 0;
+    uint64_t prof_calls[4] = {0, 0, 0, 0};
+    uint64_t prof_cells[4] = {0, 0, 0, 0};
+    double prof_ms[4] = {0, 0, 0, 0};
 };
 
 namespace swgb {

@@ -20,17 +20,32 @@ constexpr uint32_t kProfileRows = 33;  // codes 0..31 plus the pad code
 constexpr uint32_t kTileSeqs = 8;
 constexpr uint32_t kTilePairs = 4;
 
-// Arguments of the wavefront kernels (one launch = one query against one bin).
-struct WavefrontArgs {
-    // database bin
-    const uint8_t* tile_data;
-    const uint64_t* tile_off;       // per tile byte offset into tile_data
-    const uint32_t* tile_len;       // per tile padded length
-    const uint32_t* sorted_ids;     // sorted position -> original index (UINT32_MAX = empty)
+// Lanes per unit and query rows per thread of the two bins: the long
+// sequences get a warp per pair (kLongT x kLongR rows per pass), the rest
+// 8 lanes per pair (R rows per thread, chosen per query).
+constexpr int kShortT = 8;
+constexpr int kLongT = 32;
+constexpr int kLongR = 16;
+
+// One bin of units: pairs (packed 16-bit kernels) or sequences (int32), as
+// sorted positions first_unit.. or an explicit list; plus its scratch rows.
+struct BinArgs {
     uint64_t first_unit;            // first pair (or sequence) of the bin
     uint64_t n_units;               // pairs (PAIR kernels) or sequences (int32 kernels)
     const uint32_t* unit_list;      // optional: explicit sorted positions (int32 rescoring)
     const uint32_t* unit_count;     // device count for unit_list
+    uint2* boundary;                // per group slot: bstride entries of (H, E)
+    uint64_t bstride;
+};
+
+// Arguments of the search kernel (one launch = one query against the database).
+struct WavefrontArgs {
+    // database
+    const uint8_t* tile_data;
+    const uint64_t* tile_off;       // per tile byte offset into tile_data
+    const uint32_t* tile_len;       // per tile padded length
+    const uint32_t* sorted_ids;     // sorted position -> original index (UINT32_MAX = empty)
+    BinArgs bin[2];                 // 0: long sequences (or a rescoring list), 1: the rest
     // query and scoring scheme
     const uint8_t* query;
     uint32_t qlen;
@@ -41,20 +56,17 @@ struct WavefrontArgs {
     int32_t* scores;                // original order
     uint32_t* flag_list;            // sorted positions to rescore in int32
     uint32_t* flag_count;
-    // scheduling and scratch
+    // scheduling
     uint32_t* work_counter;
-    uint2* boundary;                // per group slot: bstride entries of (H, E)
-    uint64_t bstride;
     uint32_t* status;               // nonzero after an internal error
 };
 
 struct KernelChoice {
-    int T;        // threads cooperating on one pair/sequence (8, 16 or 32)
-    int R;        // query rows per thread
+    int R;        // query rows per thread in the short bin
     bool pair;    // two sequences per group in packed 16-bit lanes; else one in int32
 };
 
-// Launch one wavefront kernel over a bin. grid = 0 picks #SM x occupancy.
+// Launch the search kernel (grid = number of persistent blocks).
 cudaError_t launch_wavefront(const KernelChoice& kc, const WavefrontArgs& a, int grid,
                              cudaStream_t stream);
 // Blocks per SM the kernel reaches (for sizing scratch), and its threads per block.
@@ -81,6 +93,7 @@ struct TopkScratch {
 };
 size_t topk_scratch_bytes(uint32_t nq, uint32_t kmax, int blocks);
 void topk_scratch_carve(void* base, uint32_t nq, uint32_t kmax, int blocks, TopkScratch* s);
+int topk_launch_count();  // kernels one launch_topk call enqueues
 cudaError_t launch_topk(const int32_t* scores, uint64_t row_stride, uint64_t n, uint32_t nq,
                         uint32_t k, const TopkScratch& s, int32_t* top_scores,
                         uint64_t* top_index, cudaStream_t stream);

@@ -32,20 +32,19 @@ const int kShortR[] = {8, 12, 16, 20, 24};
 // Rows padded to whole passes times the per-step work: 6 integer operations per
 // row (5 recurrence updates and the score unpacking) plus about 12 per step.
 KernelChoice choose_short(uint32_t qlen, bool int32) {
-    if (int32) return KernelChoice{8, 16, false};
+    if (int32) return KernelChoice{16, false};
     int bestR = 16;
     double best = 1e300;
     for (int R : kShortR) {
-        const uint32_t TR = 8u * R;
+        const uint32_t TR = (uint32_t)kShortT * R;
         const double passes = (qlen + TR - 1) / TR;
         const double cost = passes * (6.0 * R + 12.0) * (R == 16 ? 0.97 : 1.0);
         if (cost < best) { best = cost; bestR = R; }
     }
-    return KernelChoice{8, bestR, true};
+    return KernelChoice{bestR, true};
 }
 
-KernelChoice choose_long(bool int32) { return int32 ? KernelChoice{32, 16, false} : KernelChoice{32, 16, true}; }
-KernelChoice rescore_choice() { return KernelChoice{32, 16, false}; }
+KernelChoice rescore_choice() { return KernelChoice{16, false}; }
 
 bool use_int32(const sw_db* db, int32_t alpha, int32_t beta) {
     return (db->flags & SW_DB_FLAG_FORCE_INT32) || (int64_t)alpha + beta > 32768;
@@ -63,26 +62,22 @@ sw_status sw_db_prepare_search(sw_db* db) {
     sw_status st;
     if ((st = db_alloc(db, (void**)&db->d_counters, 256, "search counters"))) return st;
 
-    // short bin: every kernel choice it may use (8 lanes per unit, 4 units per warp)
-    std::vector<KernelChoice> shorts;
-    for (int R : kShortR) shorts.push_back(KernelChoice{8, R, true});
-    shorts.push_back(KernelChoice{8, 16, false});
+    // one persistent grid for every kernel variant; scratch rows per group slot
+    std::vector<KernelChoice> all;
+    for (int R : kShortR) all.push_back(KernelChoice{R, true});
+    all.push_back(KernelChoice{16, false});
     const int warps = wavefront_block_threads() / 32;
+    db->grid_short = db->nsm * occupancy_max(all);
     if (db->n_long_tiles < db->n_tiles) {
-        db->grid_short = db->nsm * occupancy_max(shorts);
         db->bstride_short = 2ull * db->max_len_short;
-        const uint64_t slots = (uint64_t)db->grid_short * warps * 4;
+        const uint64_t slots = (uint64_t)db->grid_short * warps * (32 / kShortT);
         if ((st = db_alloc(db, (void**)&db->d_bnd_short, slots * db->bstride_short * sizeof(uint2),
                            "boundary rows (short)")))
             return st;
     }
     if (db->n_long_tiles) {
-        std::vector<KernelChoice> longs = {choose_long(false), choose_long(true)};
-        const uint64_t units = db->n_long_tiles * kTilePairs;
-        const int full = db->nsm * occupancy_max(longs);
-        db->grid_long = (int)std::min<uint64_t>(full, (units + warps - 1) / warps);
         db->bstride_long = 2ull * db->max_len_long;
-        const uint64_t slots = (uint64_t)db->grid_long * warps;
+        const uint64_t slots = (uint64_t)db->grid_short * warps * (32 / kLongT);
         if ((st = db_alloc(db, (void**)&db->d_bnd_long, slots * db->bstride_long * sizeof(uint2),
                            "boundary rows (long)")))
             return st;
@@ -90,7 +85,8 @@ sw_status sw_db_prepare_search(sw_db* db) {
     db->grid_rescore = std::min(kRescoreGrid, db->nsm * occupancy_max({rescore_choice()}));
     db->bstride_rescore = 2ull * std::max(4u, (db->max_len + 3u) & ~3u);
     if ((st = db_alloc(db, (void**)&db->d_bnd_rescore,
-                       (uint64_t)db->grid_rescore * warps * db->bstride_rescore * sizeof(uint2),
+                       (uint64_t)db->grid_rescore * warps * (32 / kLongT) * db->bstride_rescore *
+                           sizeof(uint2),
                        "boundary rows (rescoring)")))
         return st;
     db->topk_nq = 1;
@@ -135,7 +131,73 @@ int grid_for(const sw_db* db, const KernelChoice& kc, int cap) {
     return std::max(1, std::min(cap, db->nsm * occ));
 }
 
+cudaEvent_t take_event(sw_db* db) {
+    if (!db->event_pool.empty()) {
+        cudaEvent_t e = db->event_pool.back();
+        db->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Brackets one phase with events when the handle is profiled.
+struct PhaseTimer {
+    sw_db* db;
+    int phase;
+    cudaStream_t st;
+    uint64_t cells;
+    cudaEvent_t a = nullptr;
+    PhaseTimer(sw_db* d, int p, cudaStream_t s, uint64_t c) : db(d), phase(p), st(s), cells(c) {
+        if (db->flags & SW_DB_FLAG_PROFILE) {
+            a = take_event(db);
+            cudaEventRecord(a, st);
+        }
+    }
+    void done() {
+        if (!a) return;
+        cudaEvent_t b = take_event(db);
+        cudaEventRecord(b, st);
+        db->pending.push_back({phase, a, b, cells});
+        a = nullptr;
+    }
+};
+
 }  // namespace
+
+extern "C" sw_status sw_db_get_profile(sw_db* db, sw_profile* out) {
+    clear_error();
+    if (!db || !out) return fail(SW_ERR_INVALID_ARG, "sw_db_get_profile: NULL argument");
+    for (auto& t : db->pending) {
+        cudaError_t e = cudaEventSynchronize(t.b);
+        if (e != cudaSuccess) return cuda_fail(e, "sw_db_get_profile");
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, t.a, t.b);
+        db->prof_ms[t.phase] += ms;
+        db->prof_calls[t.phase] += 1;
+        db->prof_cells[t.phase] += t.cells;
+        db->event_pool.push_back(t.a);
+        db->event_pool.push_back(t.b);
+    }
+    db->pending.clear();
+    out->launches = db->launches;
+    for (int p = 0; p < 4; ++p) {
+        out->calls[p] = db->prof_calls[p];
+        out->cells[p] = db->prof_cells[p];
+        out->ms[p] = db->prof_ms[p];
+    }
+    return SW_OK;
+}
+
+extern "C" sw_status sw_db_reset_profile(sw_db* db) {
+    sw_profile tmp;
+    sw_status st = sw_db_get_profile(db, &tmp);
+    if (st) return st;
+    db->launches = 0;
+    for (int p = 0; p < 4; ++p) { db->prof_calls[p] = 0; db->prof_cells[p] = 0; db->prof_ms[p] = 0; }
+    return SW_OK;
+}
 
 // Enqueue one full search on `stream`. Scores land in d_scores (original order).
 sw_status enqueue_search(sw_db* db, const uint8_t* d_query, uint32_t qlen, const int8_t* d_matrix,
@@ -145,53 +207,46 @@ sw_status enqueue_search(sw_db* db, const uint8_t* d_query, uint32_t qlen, const
     const bool i32 = use_int32(db, alpha, beta);
     if ((e = cudaMemsetAsync(db->d_counters, 0, 64, stream)) != cudaSuccess)
         return cuda_fail(e, "search: counter reset");
-    const bool has_long = db->n_long_tiles > 0;
-    const bool has_short = db->n_long_tiles < db->n_tiles;
-
-    if (has_long) {
-        if ((e = cudaEventRecord(db->ev_fork, stream)) != cudaSuccess ||
-            (e = cudaStreamWaitEvent(db->stream_long, db->ev_fork, 0)) != cudaSuccess)
-            return cuda_fail(e, "search: fork");
-        WavefrontArgs a = base_args(db, d_query, qlen, d_matrix, alpha, beta, d_scores);
-        const KernelChoice kc = choose_long(i32);
-        a.first_unit = 0;
-        a.n_units = i32 ? db->n_long_tiles * kTileSeqs : db->n_long_tiles * kTilePairs;
-        a.work_counter = db->d_counters + 1;
-        a.boundary = db->d_bnd_long;
-        a.bstride = db->bstride_long;
-        if ((e = launch_wavefront(kc, a, grid_for(db, kc, db->grid_long), db->stream_long)) !=
-            cudaSuccess)
-            return cuda_fail(e, "search: long-sequence kernel");
-        if ((e = cudaEventRecord(db->ev_join, db->stream_long)) != cudaSuccess)
-            return cuda_fail(e, "search: join record");
-    }
-    if (has_short) {
+    const uint64_t per_tile = i32 ? kTileSeqs : kTilePairs;  // units per tile
+    {
         WavefrontArgs a = base_args(db, d_query, qlen, d_matrix, alpha, beta, d_scores);
         const KernelChoice kc = choose_short(qlen, i32);
-        a.first_unit = i32 ? db->n_long_tiles * kTileSeqs : db->n_long_tiles * kTilePairs;
-        a.n_units = (i32 ? kTileSeqs : kTilePairs) * (db->n_tiles - db->n_long_tiles);
+        a.bin[0].first_unit = 0;
+        a.bin[0].n_units = db->n_long_tiles * per_tile;
+        a.bin[0].boundary = db->d_bnd_long;
+        a.bin[0].bstride = db->bstride_long;
+        a.bin[1].first_unit = db->n_long_tiles * per_tile;
+        a.bin[1].n_units = (db->n_tiles - db->n_long_tiles) * per_tile;
+        a.bin[1].boundary = db->d_bnd_short;
+        a.bin[1].bstride = db->bstride_short;
         a.work_counter = db->d_counters + 0;
-        a.boundary = db->d_bnd_short;
-        a.bstride = db->bstride_short;
+        PhaseTimer pt(db, 0, stream, (uint64_t)qlen * db->total_residues);
         if ((e = launch_wavefront(kc, a, grid_for(db, kc, db->grid_short), stream)) != cudaSuccess)
-            return cuda_fail(e, "search: short-sequence kernel");
+            return cuda_fail(e, "search: wavefront kernel");
+        pt.done();
+        db->launches += 1;
     }
-    if (has_long && (e = cudaStreamWaitEvent(stream, db->ev_join, 0)) != cudaSuccess)
-        return cuda_fail(e, "search: join");
     if (!i32) {
         WavefrontArgs a = base_args(db, d_query, qlen, d_matrix, alpha, beta, d_scores);
-        a.unit_list = db->d_flags;
-        a.unit_count = db->d_counters + 3;
+        a.bin[0].unit_list = db->d_flags;
+        a.bin[0].unit_count = db->d_counters + 3;
+        a.bin[0].boundary = db->d_bnd_rescore;
+        a.bin[0].bstride = db->bstride_rescore;
+        a.bin[1].n_units = 0;
         a.work_counter = db->d_counters + 2;
-        a.boundary = db->d_bnd_rescore;
-        a.bstride = db->bstride_rescore;
+        PhaseTimer pt(db, 1, stream, 0);
         if ((e = launch_wavefront(rescore_choice(), a, db->grid_rescore, stream)) != cudaSuccess)
             return cuda_fail(e, "search: int32 rescoring kernel");
+        pt.done();
+        db->launches += 1;
     }
     if (top_k) {
+        PhaseTimer pt(db, 2, stream, 0);
         if ((e = launch_topk(d_scores, db->n_seqs, db->n_seqs, 1, top_k, db->topk, d_top_scores,
                              d_top_index, stream)) != cudaSuccess)
             return cuda_fail(e, "search: top-k");
+        pt.done();
+        db->launches += topk_launch_count();
     }
     return SW_OK;
 }

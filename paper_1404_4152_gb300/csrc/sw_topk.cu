@@ -249,6 +249,8 @@ void topk_scratch_carve(void* base, uint32_t nq, uint32_t kmax, int blocks, Topk
     s->blocks = blocks;
 }
 
+int topk_launch_count() { return 1 + 3 * 2 + 3; }
+
 cudaError_t launch_topk(const int32_t* scores, uint64_t row_stride, uint64_t n, uint32_t nq,
                         uint32_t k, const TopkScratch& s, int32_t* top_scores,
                         uint64_t* top_index, cudaStream_t stream) {

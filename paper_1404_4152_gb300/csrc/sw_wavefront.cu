@@ -114,24 +114,194 @@ __device__ __forceinline__ typename Lane::V shfl_up_v(typename Lane::V v, int T)
     return (typename Lane::V)__shfl_up_sync(0xffffffffu, (uint32_t)v, 1, T);
 }
 
+// Aligns every unit of one chunk (kWarps warps x 32/T groups) against the
+// whole query. All warps of the block process the same chunk, pass by pass.
 template <int T, int R, bool PAIR>
-__global__ void __launch_bounds__(kThreads) wavefront_kernel(const WavefrontArgs a) {
+__device__ __forceinline__ void process_chunk(const WavefrontArgs& a, const BinArgs& bin,
+                                              uint64_t base, uint64_t n_units, uint8_t* prof,
+                                              int32_t thr16) {
     using Lane = typename std::conditional<PAIR, LaneS16x2, LaneS32>::type;
     using V = typename Lane::V;
     constexpr int G = 32 / T;           // groups per warp
     constexpr int TR = T * R;           // query rows per pass
-    constexpr uint32_t UNITS = kWarps * G;
-
-    extern __shared__ __align__(16) uint8_t prof[];  // [kProfileRows][TR] int8 scores
-    __shared__ uint32_t s_chunk, s_units;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = lane / T, t = lane % T;
     const uint32_t P = (a.qlen + TR - 1) / TR;
     const uint64_t slot = ((uint64_t)blockIdx.x * kWarps + warp) * G + g;
     // two halves per slot: pass p reads half p&1 and writes the other one
-    const uint64_t half = a.bstride / 2;
-    uint2* const bnd0 = a.boundary + slot * a.bstride;
+    const uint64_t half = bin.bstride / 2;
+    uint2* const bnd0 = bin.boundary + slot * bin.bstride;
+
+    const V vbeta = Lane::splat(-a.beta);
+    const V valpha = Lane::splat(-a.alpha);
+    const V vzero = Lane::splat(0);
+    const uint32_t A = a.alphabet;
+
+    // ---- locate this group's unit ----
+    const uint64_t u = base + (uint64_t)warp * G + g;
+    const bool have = u < n_units;
+    uint64_t sp = 0;  // sorted position (first sequence of the pair)
+    uint32_t L = 0;
+    const uint8_t* stream = a.tile_data;
+    if (have) {
+        if (PAIR) sp = 2 * (bin.first_unit + u);
+        else sp = bin.unit_list ? (uint64_t)bin.unit_list[u] : bin.first_unit + u;
+        const uint64_t tile = sp / kTileSeqs;
+        const uint32_t pslot = (uint32_t)((sp >> 1) & (kTilePairs - 1));
+        L = a.tile_len[tile];
+        stream = a.tile_data + a.tile_off[tile] + pslot * 8 + (PAIR ? 0 : (sp & 1));
+    }
+    uint32_t Lw = L;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) Lw = max(Lw, __shfl_xor_sync(0xffffffffu, Lw, o));
+    const uint32_t steps = (Lw + T - 1 + 3) & ~3u;
+
+    V best = vzero;
+    for (uint32_t p = 0; p < P; ++p) {
+        __syncthreads();  // every warp is done with the previous pass's profile
+        // stage query rows [p*TR, p*TR + TR) of the profile: prof[r][k] = fsbt(q[row], r)
+        for (uint32_t idx = threadIdx.x; idx < kProfileRows * (TR / 4); idx += kThreads) {
+            const uint32_t r = idx / (TR / 4);
+            const uint32_t k4 = (idx % (TR / 4)) * 4;
+            uint32_t word = 0;
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const uint32_t row = p * TR + k4 + b;
+                int v = 0;
+                if (row < a.qlen && r < A) {
+                    const uint32_t qc = a.query[row];
+                    if (qc < A) v = a.matrix[qc * A + r];
+                }
+                word |= ((uint32_t)(uint8_t)(int8_t)v) << (8 * b);
+            }
+            reinterpret_cast<uint32_t*>(prof)[idx] = word;
+        }
+        __syncthreads();
+
+        V Hl[R], Fr[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) { Hl[r] = vzero; Fr[r] = vzero; }
+        V hb_out = vzero, eb_out = vzero, hdiag0 = vzero;
+        const bool read_bnd = (t == 0) && (p > 0);
+        const bool write_bnd = (t == T - 1) && (p + 1 < P);
+        const uint2* const bnd_in = bnd0 + (p & 1) * half;
+        uint2* const bnd_out = bnd0 + ((p + 1) & 1) * half;
+        const uint8_t* const my_rows = prof + t * R;
+
+        // codes and boundary values for the current block of 4 steps
+        uint32_t cq[4];
+        uint2 bq[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int j = k - t;
+            uint32_t c = PAIR ? (kPadCode | (kPadCode << 8)) : kPadCode;
+            if (j >= 0 && j < (int)L) {
+                const uint8_t* q = stream + (uint32_t)(j >> 2) * 32 + (j & 3) * 2;
+                c = PAIR ? (uint32_t)*reinterpret_cast<const uint16_t*>(q) : (uint32_t)*q;
+            }
+            cq[k] = c;
+            bq[k] = make_uint2(0u, 0u);
+            if (read_bnd && j < (int)L) bq[k] = bnd_in[j];
+        }
+
+        for (uint32_t s0 = 0; s0 < steps; s0 += 4) {
+            // prefetch the next block's codes and boundary row
+            uint32_t cn[4];
+            uint2 bn[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int j = (int)s0 + 4 + k - t;
+                uint32_t c = PAIR ? (kPadCode | (kPadCode << 8)) : kPadCode;
+                if (j >= 0 && j < (int)L) {
+                    const uint8_t* q = stream + (uint32_t)(j >> 2) * 32 + (j & 3) * 2;
+                    c = PAIR ? (uint32_t)*reinterpret_cast<const uint16_t*>(q) : (uint32_t)*q;
+                }
+                cn[k] = c;
+                bn[k] = make_uint2(0u, 0u);
+                if (read_bnd && j < (int)L) bn[k] = bnd_in[j];
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int j = (int)s0 + k - t;
+                // top row input: H[i0-1][j] and E[i0][j] from the thread above
+                V h_in = shfl_up_v<Lane>(hb_out, T);
+                V e_in = shfl_up_v<Lane>(eb_out, T);
+                if (t == 0) {
+                    h_in = (V)bq[k].x;
+                    e_in = (V)bq[k].y;
+                }
+                // substitution scores of this column for my R rows
+                const uint32_t ca = PAIR ? (cq[k] & 0xffu) : cq[k];
+                uint32_t wa[R / 4], wb[R / 4];
+                load_rows<R>(my_rows + ca * TR, wa);
+                if (PAIR) {
+                    load_rows<R>(my_rows + (cq[k] >> 8) * TR, wb);
+                } else {
+#pragma unroll
+                    for (int w = 0; w < R / 4; ++w) wb[w] = 0;
+                }
+                V diag = hdiag0;
+                V E = e_in;
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const V sc = Lane::score(wa[r / 4], wb[r / 4], r & 3);
+                    const V ef = Lane::vmax(E, Fr[r]);
+                    const V H = Lane::addmax_relu(diag, sc, ef);  // H[i][j]
+                    diag = Hl[r];                                  // H[i][j-1]: diagonal of row i+1
+                    Hl[r] = H;
+                    const V hb = Lane::vadd(H, vbeta);             // H[i][j] - beta
+                    E = Lane::addmax(E, valpha, hb);               // E[i+1][j]
+                    Fr[r] = Lane::addmax(Fr[r], valpha, hb);       // F[i][j+1]
+                    best = Lane::vmax(best, H);
+                }
+                hb_out = Hl[R - 1];
+                eb_out = E;
+                hdiag0 = h_in;
+                if (write_bnd && j >= 0 && j < (int)L)
+                    bnd_out[j] = make_uint2((uint32_t)hb_out, (uint32_t)eb_out);
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) { cq[k] = cn[k]; bq[k] = bn[k]; }
+        }
+    }
+
+    // ---- group maximum and results ----
+#pragma unroll
+    for (int o = T / 2; o > 0; o >>= 1)
+        best = Lane::vmax(best, (V)__shfl_xor_sync(0xffffffffu, (uint32_t)best, o, T));
+    if (have && t == 0) {
+        if (PAIR) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int32_t v = (int16_t)(h ? ((uint32_t)best >> 16) : ((uint32_t)best & 0xffffu));
+                const uint32_t id = a.sorted_ids[sp + h];
+                if (id == 0xffffffffu) continue;
+                if (v >= thr16) {
+                    const uint32_t k = atomicAdd(a.flag_count, 1u);
+                    a.flag_list[k] = (uint32_t)(sp + h);
+                } else {
+                    a.scores[id] = v;
+                }
+            }
+        } else {
+            const uint32_t id = a.sorted_ids[sp];
+            if (id != 0xffffffffu) a.scores[id] = (int32_t)best;
+        }
+    }
+}
+
+// Persistent search kernel over the two bins of a database. Chunks of bin 0
+// (the long sequences, a warp per pair: TL lanes x RL rows) are handed out
+// first, then chunks of bin 1 (TS lanes per pair x RS rows), so the longest
+// work starts first. Bin 0 may instead be an explicit list of sorted
+// positions (int32 rescoring).
+template <int TS, int RS, int TL, int RL, bool PAIR>
+__global__ void __launch_bounds__(kThreads) search_kernel(const WavefrontArgs a) {
+    extern __shared__ __align__(16) uint8_t prof[];  // [kProfileRows][rows per pass] int8
+    __shared__ uint32_t s_chunk, s_units;
+    constexpr uint32_t UNITS_L = kWarps * (32 / TL);
+    constexpr uint32_t UNITS_S = kWarps * (32 / TS);
 
     // 16-bit lanes are exact while every H stays at or below 32767 - max(0, max fsbt)
     __shared__ int s_smax;
@@ -146,198 +316,51 @@ __global__ void __launch_bounds__(kThreads) wavefront_kernel(const WavefrontArgs
     }
     const int32_t thr16 = 32767 - s_smax;
 
-    const V vbeta = Lane::splat(-a.beta);
-    const V valpha = Lane::splat(-a.alpha);
-    const V vzero = Lane::splat(0);
-    const uint32_t A = a.alphabet;
-
     for (;;) {
         if (threadIdx.x == 0) {
             s_chunk = atomicAdd(a.work_counter, 1u);
-            s_units = a.unit_list ? *a.unit_count : 0u;
+            s_units = a.bin[0].unit_list ? *a.bin[0].unit_count : 0u;
         }
         __syncthreads();
-        const uint64_t n_units = a.unit_list ? (uint64_t)s_units : a.n_units;
-        const uint64_t base = (uint64_t)s_chunk * UNITS;
-        if (base >= n_units) break;
-
-        // ---- locate this group's unit ----
-        const uint64_t u = base + (uint64_t)warp * G + g;
-        const bool have = u < n_units;
-        uint64_t sp = 0;  // sorted position (first sequence of the pair)
-        uint32_t L = 0;
-        const uint8_t* stream = a.tile_data;
-        if (have) {
-            if (PAIR) sp = 2 * (a.first_unit + u);
-            else sp = a.unit_list ? (uint64_t)a.unit_list[u] : a.first_unit + u;
-            const uint64_t tile = sp / kTileSeqs;
-            const uint32_t pslot = (uint32_t)((sp >> 1) & (kTilePairs - 1));
-            L = a.tile_len[tile];
-            stream = a.tile_data + a.tile_off[tile] + pslot * 8 + (PAIR ? 0 : (sp & 1));
+        const uint64_t n_long = a.bin[0].unit_list ? (uint64_t)s_units : a.bin[0].n_units;
+        const uint64_t chunks_long = (n_long + UNITS_L - 1) / UNITS_L;
+        const uint64_t c = s_chunk;
+        if (c < chunks_long) {
+            process_chunk<TL, RL, PAIR>(a, a.bin[0], c * UNITS_L, n_long, prof, thr16);
+        } else {
+            const uint64_t base = (c - chunks_long) * UNITS_S;
+            if (base >= a.bin[1].n_units) break;
+            process_chunk<TS, RS, PAIR>(a, a.bin[1], base, a.bin[1].n_units, prof, thr16);
         }
-        uint32_t Lw = L;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) Lw = max(Lw, __shfl_xor_sync(0xffffffffu, Lw, o));
-        const uint32_t steps = (Lw + T - 1 + 3) & ~3u;
-
-        V best = vzero;
-        for (uint32_t p = 0; p < P; ++p) {
-            __syncthreads();  // every warp is done with the previous pass's profile
-            // stage query rows [p*TR, p*TR + TR) of the profile: prof[r][k] = fsbt(q[row], r)
-            for (uint32_t idx = threadIdx.x; idx < kProfileRows * (TR / 4); idx += kThreads) {
-                const uint32_t r = idx / (TR / 4);
-                const uint32_t k4 = (idx % (TR / 4)) * 4;
-                uint32_t word = 0;
-#pragma unroll
-                for (int b = 0; b < 4; ++b) {
-                    const uint32_t row = p * TR + k4 + b;
-                    int v = 0;
-                    if (row < a.qlen && r < A) {
-                        const uint32_t qc = a.query[row];
-                        if (qc < A) v = a.matrix[qc * A + r];
-                    }
-                    word |= ((uint32_t)(uint8_t)(int8_t)v) << (8 * b);
-                }
-                reinterpret_cast<uint32_t*>(prof)[idx] = word;
-            }
-            __syncthreads();
-
-            V Hl[R], Fr[R];
-#pragma unroll
-            for (int r = 0; r < R; ++r) { Hl[r] = vzero; Fr[r] = vzero; }
-            V hb_out = vzero, eb_out = vzero, hdiag0 = vzero;
-            const bool read_bnd = (t == 0) && (p > 0);
-            const bool write_bnd = (t == T - 1) && (p + 1 < P);
-            const uint2* const bnd_in = bnd0 + (p & 1) * half;
-            uint2* const bnd_out = bnd0 + ((p + 1) & 1) * half;
-            const uint8_t* const my_rows = prof + t * R;
-
-            // codes and boundary values for the current block of 4 steps
-            uint32_t cq[4];
-            uint2 bq[4];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int j = k - t;
-                uint32_t c = PAIR ? (kPadCode | (kPadCode << 8)) : kPadCode;
-                if (j >= 0 && j < (int)L) {
-                    const uint8_t* q = stream + (uint32_t)(j >> 2) * 32 + (j & 3) * 2;
-                    c = PAIR ? (uint32_t)*reinterpret_cast<const uint16_t*>(q) : (uint32_t)*q;
-                }
-                cq[k] = c;
-                bq[k] = make_uint2(0u, 0u);
-                if (read_bnd && j < (int)L) bq[k] = bnd_in[j];
-            }
-
-            for (uint32_t s0 = 0; s0 < steps; s0 += 4) {
-                // prefetch the next block's codes and boundary row
-                uint32_t cn[4];
-                uint2 bn[4];
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const int j = (int)s0 + 4 + k - t;
-                    uint32_t c = PAIR ? (kPadCode | (kPadCode << 8)) : kPadCode;
-                    if (j >= 0 && j < (int)L) {
-                        const uint8_t* q = stream + (uint32_t)(j >> 2) * 32 + (j & 3) * 2;
-                        c = PAIR ? (uint32_t)*reinterpret_cast<const uint16_t*>(q) : (uint32_t)*q;
-                    }
-                    cn[k] = c;
-                    bn[k] = make_uint2(0u, 0u);
-                    if (read_bnd && j < (int)L) bn[k] = bnd_in[j];
-                }
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const int j = (int)s0 + k - t;
-                    // top row input: H[i0-1][j] and E[i0][j] from the thread above
-                    V h_in = shfl_up_v<Lane>(hb_out, T);
-                    V e_in = shfl_up_v<Lane>(eb_out, T);
-                    if (t == 0) {
-                        h_in = (V)bq[k].x;
-                        e_in = (V)bq[k].y;
-                    }
-                    // substitution scores of this column for my R rows
-                    const uint32_t ca = PAIR ? (cq[k] & 0xffu) : cq[k];
-                    uint32_t wa[R / 4], wb[R / 4];
-                    load_rows<R>(my_rows + ca * TR, wa);
-                    if (PAIR) {
-                        load_rows<R>(my_rows + (cq[k] >> 8) * TR, wb);
-                    } else {
-#pragma unroll
-                        for (int w = 0; w < R / 4; ++w) wb[w] = 0;
-                    }
-                    V diag = hdiag0;
-                    V E = e_in;
-#pragma unroll
-                    for (int r = 0; r < R; ++r) {
-                        const V sc = Lane::score(wa[r / 4], wb[r / 4], r & 3);
-                        const V ef = Lane::vmax(E, Fr[r]);
-                        const V H = Lane::addmax_relu(diag, sc, ef);  // H[i][j]
-                        diag = Hl[r];                                  // H[i][j-1]: diagonal of row i+1
-                        Hl[r] = H;
-                        const V hb = Lane::vadd(H, vbeta);             // H[i][j] - beta
-                        E = Lane::addmax(E, valpha, hb);               // E[i+1][j]
-                        Fr[r] = Lane::addmax(Fr[r], valpha, hb);       // F[i][j+1]
-                        best = Lane::vmax(best, H);
-                    }
-                    hb_out = Hl[R - 1];
-                    eb_out = E;
-                    hdiag0 = h_in;
-                    if (write_bnd && j >= 0 && j < (int)L)
-                        bnd_out[j] = make_uint2((uint32_t)hb_out, (uint32_t)eb_out);
-                }
-#pragma unroll
-                for (int k = 0; k < 4; ++k) { cq[k] = cn[k]; bq[k] = bn[k]; }
-            }
-        }
-
-        // ---- group maximum and results ----
-#pragma unroll
-        for (int o = T / 2; o > 0; o >>= 1)
-            best = Lane::vmax(best, (V)__shfl_xor_sync(0xffffffffu, (uint32_t)best, o, T));
-        if (have && t == 0) {
-            if (PAIR) {
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int32_t v = (int16_t)(h ? ((uint32_t)best >> 16) : ((uint32_t)best & 0xffffu));
-                    const uint32_t id = a.sorted_ids[sp + h];
-                    if (id == 0xffffffffu) continue;
-                    if (v >= thr16) {
-                        const uint32_t k = atomicAdd(a.flag_count, 1u);
-                        a.flag_list[k] = (uint32_t)(sp + h);
-                    } else {
-                        a.scores[id] = v;
-                    }
-                }
-            } else {
-                const uint32_t id = a.sorted_ids[sp];
-                if (id != 0xffffffffu) a.scores[id] = (int32_t)best;
-            }
-        }
+        __syncthreads();  // s_chunk is rewritten by the next iteration
     }
 }
 
 using KernelFn = void (*)(WavefrontArgs);
 
 struct Entry {
-    int T, R;
+    int R;
     bool pair;
     KernelFn fn;
 };
 
-#define SWGB_ENTRY(T, R, P) {T, R, P, wavefront_kernel<T, R, P>}
+#define SWGB_ENTRY(R, P) {R, P, search_kernel<kShortT, R, kLongT, kLongR, P>}
 const Entry kEntries[] = {
-    SWGB_ENTRY(8, 8, true),   SWGB_ENTRY(8, 12, true), SWGB_ENTRY(8, 16, true),
-    SWGB_ENTRY(8, 20, true),  SWGB_ENTRY(8, 24, true), SWGB_ENTRY(16, 16, true),
-    SWGB_ENTRY(32, 16, true), SWGB_ENTRY(8, 16, false), SWGB_ENTRY(32, 16, false),
+    SWGB_ENTRY(8, true),  SWGB_ENTRY(12, true), SWGB_ENTRY(16, true),
+    SWGB_ENTRY(20, true), SWGB_ENTRY(24, true), SWGB_ENTRY(16, false),
 };
 #undef SWGB_ENTRY
 
 const Entry* find_entry(const KernelChoice& kc) {
     for (const Entry& e : kEntries)
-        if (e.T == kc.T && e.R == kc.R && e.pair == kc.pair) return &e;
+        if (e.R == kc.R && e.pair == kc.pair) return &e;
     return nullptr;
 }
 
-size_t smem_bytes(const KernelChoice& kc) { return (size_t)kProfileRows * kc.T * kc.R; }
+size_t smem_bytes(const KernelChoice& kc) {
+    const int rows = kShortT * kc.R > kLongT * kLongR ? kShortT * kc.R : kLongT * kLongR;
+    return (size_t)kProfileRows * rows;
+}
 
 }  // namespace
 
