@@ -186,6 +186,44 @@ typedef struct {
 sw_status sw_db_get_profile(sw_db* db, sw_profile* out);
 sw_status sw_db_reset_profile(sw_db* db);
 
+/*
+ * Score one query against caller-owned device sequences WITHOUT allocating
+ * any device memory. The paper has no counterpart to this call; it exists for
+ * callers that may not call cudaMalloc, for example a host application that
+ * reserves all device memory up front through its own allocator and forbids
+ * other allocations, or a serving loop that cannot afford the device-wide
+ * synchronisation cudaMalloc can cause. It needs no database handle (loading
+ * one allocates): the caller passes everything as DEVICE buffers.
+ *
+ *   d_query    : DEVICE, qlen codes;  d_matrix : DEVICE, alphabet * alphabet int8
+ *   d_residues : DEVICE, the database sequences concatenated (codes < 32)
+ *   d_offsets  : DEVICE, n_seqs + 1 uint64 offsets into d_residues
+ *   max_len    : HOST value, the longest sequence in the set
+ *   d_scores   : DEVICE, n_seqs int32, written in database order
+ *   stream     : cudaStream_t as void*; the work is enqueued there
+ *
+ * Scores are the exact int32 scores of recurrence (1), identical to
+ * sw_search's. The working memory is one fixed device array of 33,554,688
+ * bytes (32 MiB + 256 B) inside the library, held by every GPU that loads the
+ * library until the process exits. It bounds the input: when qlen > 512,
+ * every sequence must be at most 2048 residues (a larger max_len is rejected
+ * with SW_ERR_INVALID_ARG; a sequence that breaks the promise gets score -1).
+ * Queries of at most 512 residues take sequences of any length.
+ *
+ * The first call on each device looks up the array's device address with
+ * cudaGetSymbolAddress (that device must be current) and caches it; make that
+ * first call before any stream capture. All calls share the array and leave
+ * their contents in it: the work counter is cleared at the start of every
+ * call, but calls whose work overlaps on the GPU (different streams, or
+ * different host threads, at the same time) race and give wrong scores.
+ * Serialise them, e.g. on one stream. The call never calls cudaMalloc,
+ * cudaFree or any allocating routine.
+ */
+sw_status sw_search_noalloc(const uint8_t* d_query, uint32_t qlen, const int8_t* d_matrix,
+                            uint32_t alphabet, int32_t alpha, int32_t beta,
+                            const uint8_t* d_residues, const uint64_t* d_offsets, uint32_t n_seqs,
+                            uint32_t max_len, int32_t* d_scores, void* stream);
+
 /* Message for the last non-OK status returned to this thread ("" if none). */
 const char* sw_last_error(void);
 

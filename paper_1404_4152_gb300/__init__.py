@@ -77,6 +77,8 @@ SIGNATURES = {
     "sw_search_device": (ctypes.c_int, [_P, _P, _U32, _P, _I32, _I32, _U32, _P, _P, _P, _P]),
     "sw_search_batch": (ctypes.c_int, [_P, _U32, _P, _P, _P, _I32, _I32, _U32, _P, _P, _P, _P,
                                        _P]),
+    "sw_search_noalloc": (ctypes.c_int, [_P, _U32, _P, _U32, _I32, _I32, _P, _P, _U32, _U32, _P,
+                                         _P]),
     "sw_db_get_profile": (ctypes.c_int, [_P, _P]),
     "sw_db_reset_profile": (ctypes.c_int, [_P]),
     "sw_last_error": (ctypes.c_char_p, []),
@@ -221,6 +223,31 @@ def sw_search_batch(db: Database, queries, matrix, alpha: int, beta: int, top_k:
                                           _ptr(nt), ctypes.byref(st)))
     return (score_rows, ts[:, :top_k], ti[:, :top_k], nt,
             {f: getattr(st, f) for f, _ in sw_stats._fields_})
+
+
+def sw_search_noalloc(d_query, qlen: int, d_matrix, alphabet: int, alpha: int, beta: int,
+                      d_residues, d_offsets, n_seqs: int, max_len: int, d_scores, stream=None):
+    """Score one query against caller-owned device sequences without any device allocation.
+
+    For callers that may not allocate device memory (their application owns the
+    whole device pool, or cannot afford cudaMalloc's synchronisation): every
+    buffer is the caller's (torch tensors or raw device pointers), and the
+    library's fixed 32 MiB scratch array does the rest. Calls that overlap on
+    the GPU share that array and race; run them one after another.
+    """
+
+    def addr(x):
+        if x is None or isinstance(x, int):
+            return x
+        return x.data_ptr()
+
+    s = stream
+    if s is not None and not isinstance(s, int):
+        s = s.cuda_stream
+    _check(load_library().sw_search_noalloc(addr(d_query), int(qlen), addr(d_matrix), int(alphabet),
+                                            int(alpha), int(beta), addr(d_residues),
+                                            addr(d_offsets), int(n_seqs), int(max_len),
+                                            addr(d_scores), s))
 
 
 def sw_db_get_profile(db: Database) -> dict:
