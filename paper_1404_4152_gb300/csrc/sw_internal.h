@@ -34,8 +34,8 @@ struct BinArgs {
     uint64_t n_units;               // pairs (PAIR kernels) or sequences (int32 kernels)
     const uint32_t* unit_list;      // optional: explicit sorted positions (int32 rescoring)
     const uint32_t* unit_count;     // device count for unit_list
-    uint2* boundary;                // per group slot: bstride entries of (H, E)
-    uint64_t bstride;
+    uint2* boundary;                // per group slot: two halves of bstride/2 entries of (H, E)
+    uint64_t bstride;               // a multiple of 8
 };
 
 // Arguments of the search kernel (one launch = one query against the database).
@@ -65,6 +65,10 @@ struct KernelChoice {
     int R;        // query rows per thread in the short bin
     bool pair;    // two sequences per group in packed 16-bit lanes; else one in int32
 };
+
+// Entries past a unit's length that a boundary row half must hold (per half:
+// length + boundary_slack(), rounded up to a multiple of 4).
+uint32_t boundary_slack();
 
 // Launch the search kernel (grid = number of persistent blocks).
 cudaError_t launch_wavefront(const KernelChoice& kc, const WavefrontArgs& a, int grid,

@@ -29,8 +29,8 @@ constexpr int kRescoreGrid = 64;
 
 const int kShortR[] = {8, 12, 16, 20, 24};
 
-// Rows padded to whole passes times the per-step work: 6 integer operations per
-// row (5 recurrence updates and the score unpacking) plus about 12 per step.
+// Rows padded to whole passes times the per-step work: 4.5 ALU operations per
+// row plus about 8 per step.
 KernelChoice choose_short(uint32_t qlen, bool int32) {
     if (int32) return KernelChoice{16, false};
     int bestR = 16;
@@ -38,7 +38,7 @@ KernelChoice choose_short(uint32_t qlen, bool int32) {
     for (int R : kShortR) {
         const uint32_t TR = (uint32_t)kShortT * R;
         const double passes = (qlen + TR - 1) / TR;
-        const double cost = passes * (6.0 * R + 12.0) * (R == 16 ? 0.97 : 1.0);
+        const double cost = passes * (4.5 * R + 8.0) * (R == 16 ? 0.97 : 1.0);
         if (cost < best) { best = cost; bestR = R; }
     }
     return KernelChoice{bestR, true};
@@ -48,6 +48,12 @@ KernelChoice rescore_choice() { return KernelChoice{16, false}; }
 
 bool use_int32(const sw_db* db, int32_t alpha, int32_t beta) {
     return (db->flags & SW_DB_FLAG_FORCE_INT32) || (int64_t)alpha + beta > 32768;
+}
+
+// Two halves per slot, each the longest unit plus the wavefront's slack.
+uint64_t bstride_for(uint32_t max_len) {
+    const uint64_t half = ((uint64_t)max_len + boundary_slack() + 3) & ~3ull;
+    return 2 * half;
 }
 
 int occupancy_max(const std::vector<KernelChoice>& cs) {
@@ -69,21 +75,21 @@ sw_status sw_db_prepare_search(sw_db* db) {
     const int warps = wavefront_block_threads() / 32;
     db->grid_short = db->nsm * occupancy_max(all);
     if (db->n_long_tiles < db->n_tiles) {
-        db->bstride_short = 2ull * db->max_len_short;
+        db->bstride_short = bstride_for(db->max_len_short);
         const uint64_t slots = (uint64_t)db->grid_short * warps * (32 / kShortT);
         if ((st = db_alloc(db, (void**)&db->d_bnd_short, slots * db->bstride_short * sizeof(uint2),
                            "boundary rows (short)")))
             return st;
     }
     if (db->n_long_tiles) {
-        db->bstride_long = 2ull * db->max_len_long;
+        db->bstride_long = bstride_for(db->max_len_long);
         const uint64_t slots = (uint64_t)db->grid_short * warps * (32 / kLongT);
         if ((st = db_alloc(db, (void**)&db->d_bnd_long, slots * db->bstride_long * sizeof(uint2),
                            "boundary rows (long)")))
             return st;
     }
     db->grid_rescore = std::min(kRescoreGrid, db->nsm * occupancy_max({rescore_choice()}));
-    db->bstride_rescore = 2ull * std::max(4u, (db->max_len + 3u) & ~3u);
+    db->bstride_rescore = bstride_for(std::max(4u, (db->max_len + 3u) & ~3u));
     if ((st = db_alloc(db, (void**)&db->d_bnd_rescore,
                        (uint64_t)db->grid_rescore * warps * (32 / kLongT) * db->bstride_rescore *
                            sizeof(uint2),

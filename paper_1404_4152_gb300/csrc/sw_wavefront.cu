@@ -10,12 +10,18 @@
 //    the linear-space rows of Section III.A). The database sequence streams
 //    through the group one column per step; thread t works on column s - t at
 //    step s, so the group sweeps an anti-diagonal band (the minor-diagonal
-//    pattern cited in Section I) and hands the bottom row's H and E to the
-//    next thread with a warp shuffle.
+//    pattern cited in Section I) and hands the bottom row's H and E, and the
+//    residue codes of the column, to the next thread with warp shuffles.
 //  - A pass covers T*R query rows. Between passes the bottom row is kept in a
 //    global scratch row (the paper's tiled computation, Section IV.C; two
 //    halves per group, read one / write the other) and the block stages the
 //    next T*R rows of the query profile (Section III.B.2) in shared memory.
+//  - The integer ALU pipe is the bottleneck (every max, fused add-max and
+//    byte permute runs there; plain 16x2 adds run on the FMA pipe), so the
+//    cell update is written to keep ALU work at 4.5 instructions per cell
+//    pair: unpack the two int8 scores (prmt), H = max3(diag + s, E, F, 0)
+//    with the add on the FMA pipe, E and F as fused add-max, and the running
+//    maximum fused two rows at a time.
 //  - Exactness: 16-bit lanes wrap, so a lane whose maximum reaches
 //    thr16 = 32767 - max(0, max fsbt) is flagged and rescored by the int32
 //    kernel. Below that threshold no intermediate can leave the 16-bit range
@@ -41,7 +47,6 @@ __device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
     asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(sel));
     return d;
 }
-
 // Packed pair of 16-bit lanes: low half = first sequence, high half = second.
 struct LaneS16x2 {
     using V = uint32_t;
@@ -65,12 +70,8 @@ struct LaneS16x2 {
     }
     // max(a + b, c) per lane
     static __device__ __forceinline__ V addmax(V a, V b, V c) { return __viaddmax_s16x2(a, b, c); }
-    // substitution scores of row b of a 4-row int8 word, for both sequences,
-    // sign-extended into the two 16-bit lanes
-    static __device__ __forceinline__ V score(uint32_t wa, uint32_t wb, int b) {
-        const uint32_t sel = (uint32_t)b | ((8u | b) << 4) | ((4u + b) << 8) | ((12u + b) << 12);
-        return prmt(wa, wb, sel);
-    }
+    // max(a, b, c, 0) per lane
+    static __device__ __forceinline__ V max3_relu(V a, V b, V c) { return __vimax3_s16x2_relu(a, b, c); }
 };
 
 // One sequence in a 32-bit lane.
@@ -83,9 +84,36 @@ struct LaneS32 {
         return __viaddmax_s32_relu(a, b, c);
     }
     static __device__ __forceinline__ V addmax(V a, V b, V c) { return __viaddmax_s32(a, b, c); }
-    static __device__ __forceinline__ V score(uint32_t wa, uint32_t, int b) {
-        const uint32_t s = 8u | b;
-        return (V)prmt(wa, 0u, (uint32_t)b | (s << 4) | (s << 8) | (s << 12));
+    static __device__ __forceinline__ V max3_relu(V a, V b, V c) { return __vimax3_s32_relu(a, b, c); }
+};
+
+// fsbt(q[row], r) for one query row, 0 outside the query or the alphabet.
+__device__ __forceinline__ int profile_score(const WavefrontArgs& a, uint32_t row, uint32_t r) {
+    if (row >= a.qlen || r >= a.alphabet) return 0;
+    const uint32_t qc = a.query[row];
+    return qc < a.alphabet ? (int)a.matrix[qc * a.alphabet + r] : 0;
+}
+
+// Query profile of one pass in shared memory: prof[r][k] = fsbt(q[p*T*R + k], r)
+// as int8, r = 0..32 (32 = pad code, all zero). Thread t reads its R rows for
+// one code as R contiguous bytes at r * T*R + t * R.
+template <int T, int R, bool PAIR>
+struct Profile {
+    static constexpr int TR = T * R;
+    static constexpr size_t kBytes = (size_t)kProfileRows * TR;
+
+    static __device__ __forceinline__ void stage(uint8_t* prof, const WavefrontArgs& a, uint32_t p) {
+        for (uint32_t idx = threadIdx.x; idx < kProfileRows * (TR / 4); idx += kThreads) {
+            const uint32_t r = idx / (TR / 4);
+            const uint32_t k4 = (idx % (TR / 4)) * 4;
+            uint32_t word = 0;
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const int v = profile_score(a, p * TR + k4 + b, r);
+                word |= ((uint32_t)(uint8_t)(int8_t)v) << (8 * b);
+            }
+            reinterpret_cast<uint32_t*>(prof)[idx] = word;
+        }
     }
 };
 
@@ -109,13 +137,39 @@ __device__ __forceinline__ void load_rows(const uint8_t* p, uint32_t (&w)[R / 4]
     }
 }
 
-template <class Lane>
-__device__ __forceinline__ typename Lane::V shfl_up_v(typename Lane::V v, int T) {
-    return (typename Lane::V)__shfl_up_sync(0xffffffffu, (uint32_t)v, 1, T);
-}
+// Substitution scores of one column for a thread's R rows, as lane words.
+template <int T, int R, bool PAIR>
+struct ColumnScores {
+    using Lane = typename std::conditional<PAIR, LaneS16x2, LaneS32>::type;
+    using V = typename Lane::V;
+    uint32_t wa[R / 4], wb[PAIR ? R / 4 : 1];
+
+    __device__ __forceinline__ void load(const uint8_t* prof, uint32_t ca, uint32_t cb, int t) {
+        const uint8_t* my_rows = prof + t * R;
+        load_rows<R>(my_rows + ca * (T * R), wa);
+        if (PAIR) load_rows<R>(my_rows + cb * (T * R), reinterpret_cast<uint32_t(&)[R / 4]>(wb));
+    }
+    // row l: both sequences' int8 scores sign-extended into the two 16-bit
+    // lanes (pair), or the int32 score
+    __device__ __forceinline__ V row(int l) const {
+        const uint32_t b = (uint32_t)(l & 3);
+        if (PAIR) {
+            return prmt(wa[l / 4], wb[l / 4], b | ((8u | b) << 4) | ((4u + b) << 8) | ((12u + b) << 12));
+        } else {
+            const uint32_t x = 8u | b;
+            return (V)prmt(wa[l / 4], 0u, b | (x << 4) | (x << 8) | (x << 12));
+        }
+    }
+};
 
 // Aligns every unit of one chunk (kWarps warps x 32/T groups) against the
 // whole query. All warps of the block process the same chunk, pass by pass.
+//
+// Boundary rows: entry T + j of a slot half holds (H, E) of column j (entries
+// below T take the fill steps' writes and are never read). Thread 0 reads them
+// in aligned 4-column blocks; blocks at or past the unit's length L (a
+// multiple of 4) read as zero, which is safe for the pad columns there: every
+// value they produce stays at or below the largest real H.
 template <int T, int R, bool PAIR>
 __device__ __forceinline__ void process_chunk(const WavefrontArgs& a, const BinArgs& bin,
                                               uint64_t base, uint64_t n_units, uint8_t* prof,
@@ -124,19 +178,19 @@ __device__ __forceinline__ void process_chunk(const WavefrontArgs& a, const BinA
     using V = typename Lane::V;
     constexpr int G = 32 / T;           // groups per warp
     constexpr int TR = T * R;           // query rows per pass
+    constexpr uint32_t kPadPair = kPadCode | (kPadCode << 8);
+    constexpr uint32_t kPadWord = kPadPair | (kPadPair << 16);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = lane / T, t = lane % T;
     const uint32_t P = (a.qlen + TR - 1) / TR;
     const uint64_t slot = ((uint64_t)blockIdx.x * kWarps + warp) * G + g;
-    // two halves per slot: pass p reads half p&1 and writes the other one
     const uint64_t half = bin.bstride / 2;
     uint2* const bnd0 = bin.boundary + slot * bin.bstride;
 
     const V vbeta = Lane::splat(-a.beta);
     const V valpha = Lane::splat(-a.alpha);
     const V vzero = Lane::splat(0);
-    const uint32_t A = a.alphabet;
 
     // ---- locate this group's unit ----
     const uint64_t u = base + (uint64_t)warp * G + g;
@@ -144,110 +198,82 @@ __device__ __forceinline__ void process_chunk(const WavefrontArgs& a, const BinA
     uint64_t sp = 0;  // sorted position (first sequence of the pair)
     uint32_t L = 0;
     const uint8_t* stream = a.tile_data;
+    uint32_t half_sel = 0;  // int32 lanes: which sequence of the pair stream
     if (have) {
         if (PAIR) sp = 2 * (bin.first_unit + u);
         else sp = bin.unit_list ? (uint64_t)bin.unit_list[u] : bin.first_unit + u;
         const uint64_t tile = sp / kTileSeqs;
         const uint32_t pslot = (uint32_t)((sp >> 1) & (kTilePairs - 1));
         L = a.tile_len[tile];
-        stream = a.tile_data + a.tile_off[tile] + pslot * 8 + (PAIR ? 0 : (sp & 1));
+        stream = a.tile_data + a.tile_off[tile] + pslot * 8;
+        half_sel = (uint32_t)(sp & 1);
     }
     uint32_t Lw = L;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) Lw = max(Lw, __shfl_xor_sync(0xffffffffu, Lw, o));
     const uint32_t steps = (Lw + T - 1 + 3) & ~3u;
+    const uint32_t blocks_real = L / 4;  // 4-column blocks of this unit (L is a multiple of 4)
 
     V best = vzero;
     for (uint32_t p = 0; p < P; ++p) {
         __syncthreads();  // every warp is done with the previous pass's profile
-        // stage query rows [p*TR, p*TR + TR) of the profile: prof[r][k] = fsbt(q[row], r)
-        for (uint32_t idx = threadIdx.x; idx < kProfileRows * (TR / 4); idx += kThreads) {
-            const uint32_t r = idx / (TR / 4);
-            const uint32_t k4 = (idx % (TR / 4)) * 4;
-            uint32_t word = 0;
-#pragma unroll
-            for (int b = 0; b < 4; ++b) {
-                const uint32_t row = p * TR + k4 + b;
-                int v = 0;
-                if (row < a.qlen && r < A) {
-                    const uint32_t qc = a.query[row];
-                    if (qc < A) v = a.matrix[qc * A + r];
-                }
-                word |= ((uint32_t)(uint8_t)(int8_t)v) << (8 * b);
-            }
-            reinterpret_cast<uint32_t*>(prof)[idx] = word;
-        }
+        Profile<T, R, PAIR>::stage(prof, a, p);
         __syncthreads();
 
         V Hl[R], Fr[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) { Hl[r] = vzero; Fr[r] = vzero; }
         V hb_out = vzero, eb_out = vzero, hdiag0 = vzero;
-        const bool read_bnd = (t == 0) && (p > 0);
-        const bool write_bnd = (t == T - 1) && (p + 1 < P);
-        const uint2* const bnd_in = bnd0 + (p & 1) * half;
-        uint2* const bnd_out = bnd0 + ((p + 1) & 1) * half;
-        const uint8_t* const my_rows = prof + t * R;
+        uint32_t code_out = PAIR ? kPadPair : kPadCode;
+        const uint2* const bnd_in = bnd0 + (p & 1) * half + T;
+        uint2* const bnd_out = bnd0 + ((p + 1) & 1) * half + T;
+        const bool read_bnd = p > 0;
 
-        // codes and boundary values for the current block of 4 steps
-        uint32_t cq[4];
-        uint2 bq[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int j = k - t;
-            uint32_t c = PAIR ? (kPadCode | (kPadCode << 8)) : kPadCode;
-            if (j >= 0 && j < (int)L) {
-                const uint8_t* q = stream + (uint32_t)(j >> 2) * 32 + (j & 3) * 2;
-                c = PAIR ? (uint32_t)*reinterpret_cast<const uint16_t*>(q) : (uint32_t)*q;
+        // thread 0's codes (4 columns per 8-byte word) and boundary values, one block ahead
+        uint2 wq = make_uint2(kPadWord, kPadWord);
+        uint4 bq0 = make_uint4(0, 0, 0, 0), bq1 = make_uint4(0, 0, 0, 0);
+        if (t == 0 && blocks_real > 0) {
+            wq = *reinterpret_cast<const uint2*>(stream);
+            if (read_bnd) {
+                bq0 = reinterpret_cast<const uint4*>(bnd_in)[0];
+                bq1 = reinterpret_cast<const uint4*>(bnd_in)[1];
             }
-            cq[k] = c;
-            bq[k] = make_uint2(0u, 0u);
-            if (read_bnd && j < (int)L) bq[k] = bnd_in[j];
         }
 
         for (uint32_t s0 = 0; s0 < steps; s0 += 4) {
-            // prefetch the next block's codes and boundary row
-            uint32_t cn[4];
-            uint2 bn[4];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int j = (int)s0 + 4 + k - t;
-                uint32_t c = PAIR ? (kPadCode | (kPadCode << 8)) : kPadCode;
-                if (j >= 0 && j < (int)L) {
-                    const uint8_t* q = stream + (uint32_t)(j >> 2) * 32 + (j & 3) * 2;
-                    c = PAIR ? (uint32_t)*reinterpret_cast<const uint16_t*>(q) : (uint32_t)*q;
+            uint2 wn = make_uint2(kPadWord, kPadWord);
+            uint4 bn0 = make_uint4(0, 0, 0, 0), bn1 = make_uint4(0, 0, 0, 0);
+            const uint32_t nb = (s0 >> 2) + 1;
+            if (t == 0 && nb < blocks_real) {
+                wn = *reinterpret_cast<const uint2*>(stream + (size_t)nb * 32);
+                if (read_bnd) {
+                    bn0 = reinterpret_cast<const uint4*>(bnd_in + s0 + 4)[0];
+                    bn1 = reinterpret_cast<const uint4*>(bnd_in + s0 + 4)[1];
                 }
-                cn[k] = c;
-                bn[k] = make_uint2(0u, 0u);
-                if (read_bnd && j < (int)L) bn[k] = bnd_in[j];
             }
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                const int j = (int)s0 + k - t;
-                // top row input: H[i0-1][j] and E[i0][j] from the thread above
-                V h_in = shfl_up_v<Lane>(hb_out, T);
-                V e_in = shfl_up_v<Lane>(eb_out, T);
+                // inputs from the thread above: its previous step's bottom row and codes
+                V h_in = (V)__shfl_up_sync(0xffffffffu, (uint32_t)hb_out, 1, T);
+                V e_in = (V)__shfl_up_sync(0xffffffffu, (uint32_t)eb_out, 1, T);
+                uint32_t code = __shfl_up_sync(0xffffffffu, code_out, 1, T);
                 if (t == 0) {
-                    h_in = (V)bq[k].x;
-                    e_in = (V)bq[k].y;
+                    const uint32_t w = (k < 2) ? wq.x : wq.y;
+                    code = PAIR ? ((w >> (16 * (k & 1))) & 0xffffu)
+                                : ((w >> (16 * (k & 1) + 8 * half_sel)) & 0xffu);
+                    const uint4& bq = (k < 2) ? bq0 : bq1;
+                    h_in = (V)((k & 1) ? bq.z : bq.x);
+                    e_in = (V)((k & 1) ? bq.w : bq.y);
                 }
-                // substitution scores of this column for my R rows
-                const uint32_t ca = PAIR ? (cq[k] & 0xffu) : cq[k];
-                uint32_t wa[R / 4], wb[R / 4];
-                load_rows<R>(my_rows + ca * TR, wa);
-                if (PAIR) {
-                    load_rows<R>(my_rows + (cq[k] >> 8) * TR, wb);
-                } else {
-#pragma unroll
-                    for (int w = 0; w < R / 4; ++w) wb[w] = 0;
-                }
+                code_out = code;
+                ColumnScores<T, R, PAIR> cs;
+                cs.load(prof, PAIR ? (code & 0xffu) : code, code >> 8, t);
                 V diag = hdiag0;
                 V E = e_in;
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
-                    const V sc = Lane::score(wa[r / 4], wb[r / 4], r & 3);
-                    const V ef = Lane::vmax(E, Fr[r]);
-                    const V H = Lane::addmax_relu(diag, sc, ef);  // H[i][j]
+                    const V sc = cs.row(r);
+                    const V H = Lane::max3_relu(Lane::vadd(diag, sc), E, Fr[r]);  // H[i][j]
                     diag = Hl[r];                                  // H[i][j-1]: diagonal of row i+1
                     Hl[r] = H;
                     const V hb = Lane::vadd(H, vbeta);             // H[i][j] - beta
@@ -258,11 +284,12 @@ __device__ __forceinline__ void process_chunk(const WavefrontArgs& a, const BinA
                 hb_out = Hl[R - 1];
                 eb_out = E;
                 hdiag0 = h_in;
-                if (write_bnd && j >= 0 && j < (int)L)
-                    bnd_out[j] = make_uint2((uint32_t)hb_out, (uint32_t)eb_out);
+                if (t == T - 1)  // column s - (T-1), at entry T + that >= 1
+                    bnd_out[(int)(s0 + k) - (T - 1)] = make_uint2((uint32_t)hb_out, (uint32_t)eb_out);
             }
-#pragma unroll
-            for (int k = 0; k < 4; ++k) { cq[k] = cn[k]; bq[k] = bn[k]; }
+            wq = wn;
+            bq0 = bn0;
+            bq1 = bn1;
         }
     }
 
@@ -298,7 +325,7 @@ __device__ __forceinline__ void process_chunk(const WavefrontArgs& a, const BinA
 // positions (int32 rescoring).
 template <int TS, int RS, int TL, int RL, bool PAIR>
 __global__ void __launch_bounds__(kThreads) search_kernel(const WavefrontArgs a) {
-    extern __shared__ __align__(16) uint8_t prof[];  // [kProfileRows][rows per pass] int8
+    extern __shared__ __align__(16) uint8_t prof[];
     __shared__ uint32_t s_chunk, s_units;
     constexpr uint32_t UNITS_L = kWarps * (32 / TL);
     constexpr uint32_t UNITS_S = kWarps * (32 / TS);
@@ -342,9 +369,14 @@ struct Entry {
     int R;
     bool pair;
     KernelFn fn;
+    size_t smem;
 };
 
-#define SWGB_ENTRY(R, P) {R, P, search_kernel<kShortT, R, kLongT, kLongR, P>}
+#define SWGB_ENTRY(R, P)                                                           \
+    {R, P, search_kernel<kShortT, R, kLongT, kLongR, P>,                           \
+     (Profile<kShortT, R, P>::kBytes > Profile<kLongT, kLongR, P>::kBytes         \
+          ? Profile<kShortT, R, P>::kBytes                                         \
+          : Profile<kLongT, kLongR, P>::kBytes)}
 const Entry kEntries[] = {
     SWGB_ENTRY(8, true),  SWGB_ENTRY(12, true), SWGB_ENTRY(16, true),
     SWGB_ENTRY(20, true), SWGB_ENTRY(24, true), SWGB_ENTRY(16, false),
@@ -357,11 +389,6 @@ const Entry* find_entry(const KernelChoice& kc) {
     return nullptr;
 }
 
-size_t smem_bytes(const KernelChoice& kc) {
-    const int rows = kShortT * kc.R > kLongT * kLongR ? kShortT * kc.R : kLongT * kLongR;
-    return (size_t)kProfileRows * rows;
-}
-
 }  // namespace
 
 bool wavefront_supported(const KernelChoice& kc) { return find_entry(kc) != nullptr; }
@@ -371,8 +398,12 @@ int wavefront_occupancy(const KernelChoice& kc, int* threads_per_block) {
     const Entry* e = find_entry(kc);
     if (threads_per_block) *threads_per_block = kThreads;
     if (!e) return 0;
+    if (e->smem > 48 * 1024 &&
+        cudaFuncSetAttribute(e->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)e->smem) !=
+            cudaSuccess)
+        return 0;
     int blocks = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, e->fn, kThreads, smem_bytes(kc)) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, e->fn, kThreads, e->smem) !=
         cudaSuccess)
         return 0;
     return blocks;
@@ -383,9 +414,18 @@ cudaError_t launch_wavefront(const KernelChoice& kc, const WavefrontArgs& a, int
     const Entry* e = find_entry(kc);
     if (!e) return cudaErrorInvalidValue;
     if (grid <= 0) return cudaErrorInvalidConfiguration;
-    e->fn<<<grid, kThreads, smem_bytes(kc), stream>>>(a);
+    if (e->smem > 48 * 1024) {
+        cudaError_t err =
+            cudaFuncSetAttribute(e->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)e->smem);
+        if (err != cudaSuccess) return err;
+    }
+    e->fn<<<grid, kThreads, e->smem, stream>>>(a);
     return cudaGetLastError();
 }
+
+// Longest pad needed past a unit's last column by the boundary rows.
+uint32_t boundary_slack() { return 2 * kLongT + 8; }
+
 
 // ---------------------------------------------------------------------------
 // Database layout kernels
