@@ -187,6 +187,30 @@ sw_status sw_db_get_profile(sw_db* db, sw_profile* out);
 sw_status sw_db_reset_profile(sw_db* db);
 
 /*
+ * Search nq queries with DEVICE buffers in one batched launch sequence,
+ * enqueued on a caller stream (cudaStream_t as void*).
+ *
+ *   d_queries    : DEVICE, all queries concatenated
+ *   qoffsets     : HOST, nq + 1 ascending offsets into d_queries (query q is
+ *                  d_queries[qoffsets[q] .. qoffsets[q+1]), at least 1 residue)
+ *   d_matrix     : DEVICE, alphabet * alphabet int8
+ *   d_scores     : DEVICE, nq * n_seqs int32, row q = query q, database order
+ *   d_top_scores : DEVICE, nq * top_k int32; d_top_index : DEVICE, nq * top_k uint64
+ *
+ * Queries are paired by length and each pair shares the 16-bit halves of the
+ * lanes; all pairs run in one persistent launch. The launch sequence is
+ * captured in a CUDA graph and replayed when the next call has the same
+ * buffers, lengths, penalties and stream. The call returns after enqueueing.
+ * If more (query, sequence) pairs saturate the 16-bit lanes than the
+ * rescoring list holds (max(n_seqs, 2^20) entries), the excess keep the score
+ * -1; sw_search_batch detects this and searches again in int32.
+ */
+sw_status sw_search_batch_device(sw_db* db, uint32_t nq, const uint8_t* d_queries,
+                                 const uint64_t* qoffsets, const int8_t* d_matrix, int32_t alpha,
+                                 int32_t beta, uint32_t top_k, int32_t* d_scores,
+                                 int32_t* d_top_scores, uint64_t* d_top_index, void* stream);
+
+/*
  * Score one query against caller-owned device sequences WITHOUT allocating
  * any device memory. The paper has no counterpart to this call; it exists for
  * callers that may not call cudaMalloc, for example a host application that

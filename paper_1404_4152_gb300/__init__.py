@@ -77,6 +77,8 @@ SIGNATURES = {
     "sw_search_device": (ctypes.c_int, [_P, _P, _U32, _P, _I32, _I32, _U32, _P, _P, _P, _P]),
     "sw_search_batch": (ctypes.c_int, [_P, _U32, _P, _P, _P, _I32, _I32, _U32, _P, _P, _P, _P,
                                        _P]),
+    "sw_search_batch_device": (ctypes.c_int, [_P, _U32, _P, _P, _P, _I32, _I32, _U32, _P, _P, _P,
+                                              _P]),
     "sw_search_noalloc": (ctypes.c_int, [_P, _U32, _P, _U32, _I32, _I32, _P, _P, _U32, _U32, _P,
                                          _P]),
     "sw_db_get_profile": (ctypes.c_int, [_P, _P]),
@@ -223,6 +225,25 @@ def sw_search_batch(db: Database, queries, matrix, alpha: int, beta: int, top_k:
                                           _ptr(nt), ctypes.byref(st)))
     return (score_rows, ts[:, :top_k], ti[:, :top_k], nt,
             {f: getattr(st, f) for f, _ in sw_stats._fields_})
+
+
+def sw_search_batch_device(db: Database, d_queries, qoffsets, d_matrix, alpha: int, beta: int,
+                           top_k: int, d_scores, d_top_scores, d_top_index, stream=None):
+    """Batch on DEVICE buffers: d_queries concatenated, qoffsets (host, nq+1), d_scores [nq, n]."""
+
+    def addr(x):
+        if x is None or isinstance(x, int):
+            return x
+        return x.data_ptr()
+
+    off = np.ascontiguousarray(qoffsets, dtype=np.uint64)
+    s = stream
+    if s is not None and not isinstance(s, int):
+        s = s.cuda_stream
+    _check(load_library().sw_search_batch_device(db.handle, off.size - 1, addr(d_queries),
+                                                 _ptr(off), addr(d_matrix), int(alpha), int(beta),
+                                                 int(top_k), addr(d_scores), addr(d_top_scores),
+                                                 addr(d_top_index), s))
 
 
 def sw_search_noalloc(d_query, qlen: int, d_matrix, alphabet: int, alpha: int, beta: int,

@@ -114,6 +114,10 @@ void release(sw_db* db) {
     if (db->ev_t0) cudaEventDestroy(db->ev_t0);
     if (db->ev_t1) cudaEventDestroy(db->ev_t1);
     if (db->h_pinned) cudaFreeHost(db->h_pinned);
+    if (db->graph.exec) cudaGraphExecDestroy(db->graph.exec);
+    for (DevBuf* b : {&db->b_pairs, &db->b_qoff, &db->b_qlen, &db->b_flags, &db->b_topk,
+                      &db->b_queries, &db->b_scores, &db->b_top})
+        db_free(db, b->p, b->cap);
     for (auto& t : db->pending) { cudaEventDestroy(t.a); cudaEventDestroy(t.b); }
     for (auto ev : db->event_pool) cudaEventDestroy(ev);
     delete db;
@@ -288,8 +292,7 @@ extern "C" sw_status sw_db_load(const uint8_t* residues, const uint64_t* offsets
         (st = db_alloc(db, (void**)&db->d_tile_len, n_tiles * 4, "sw_db_load: tile lengths")) ||
         (st = db_alloc(db, (void**)&db->d_sorted, n_tiles * kTileSeqs * 4,
                        "sw_db_load: sorted ids")) ||
-        (st = db_alloc(db, (void**)&db->d_scores, n_seqs * 4, "sw_db_load: score buffer")) ||
-        (st = db_alloc(db, (void**)&db->d_flags, n_seqs * 4, "sw_db_load: rescoring list"))) {
+        (st = db_alloc(db, (void**)&db->d_scores, n_seqs * 4, "sw_db_load: score buffer"))) {
         cleanup_raw();
         release(db);
         return st;

@@ -11,6 +11,33 @@
 #include "sw.h"
 #include "sw_internal.h"
 
+// Grow-only device buffer owned by a handle.
+struct DevBuf {
+    void* p = nullptr;
+    size_t cap = 0;
+};
+
+// The captured launch sequence of the last batch and what it baked in.
+struct BatchGraph {
+    cudaGraphExec_t exec = nullptr;
+    const void* queries = nullptr;
+    const void* matrix = nullptr;
+    const void* scores = nullptr;
+    const void* top_s = nullptr;
+    const void* top_i = nullptr;
+    int32_t alpha = 0, beta = 0;
+    uint32_t top_k = 0;
+    cudaStream_t stream = nullptr;
+    std::vector<uint64_t> qoff;
+    std::vector<uint32_t> qlen;
+    uint32_t kernels = 0;
+};
+
+struct BatchInfo {
+    uint64_t cells = 0;
+    uint32_t flag_cap = 0;  // 0: the batch ran in int32 (no rescoring list)
+};
+
 struct sw_db {
     // identity
     int device = 0;
@@ -38,7 +65,8 @@ struct sw_db {
     uint32_t* d_tile_len = nullptr;
     uint32_t* d_sorted = nullptr;  // sorted position -> original index
     int32_t* d_scores = nullptr;   // internal score row (original order)
-    uint32_t* d_flags = nullptr;   // sorted positions rescored in int32
+    uint32_t* d_flags = nullptr;   // unused
+    uint2* d_flags2 = nullptr;     // (query row, sorted position) rescored in int32
     uint32_t* d_misc = nullptr;
 
     // search scratch
@@ -63,6 +91,10 @@ struct sw_db {
     void* h_pinned = nullptr;
 
     std::vector<std::pair<void*, size_t>> allocs;
+
+    // batch buffers (grown on demand) and the captured batch graph
+    DevBuf b_pairs, b_qoff, b_qlen, b_flags, b_topk, b_queries, b_scores, b_top;
+    BatchGraph graph;
 
     // residues of the sequences in each bin (for cell counts)
     uint64_t residues_short = 0, residues_long = 0;
@@ -94,3 +126,12 @@ sw_status db_alloc(sw_db* db, void** p, size_t bytes, const char* what);
 
 // Allocate the per-handle search scratch (boundary rows, counters, top-k).
 sw_status sw_db_prepare_search(sw_db* db);
+sw_status ensure(sw_db* db, DevBuf& b, size_t bytes, const char* what);
+// Enqueue a whole single-query search / batch on a stream (sw_search.cu).
+sw_status enqueue_search(sw_db* db, const uint8_t* d_query, uint32_t qlen, const int8_t* d_matrix,
+                         int32_t alpha, int32_t beta, uint32_t top_k, int32_t* d_scores,
+                         int32_t* d_top_scores, uint64_t* d_top_index, cudaStream_t stream);
+sw_status enqueue_batch(sw_db* db, uint32_t nq, const uint8_t* d_queries,
+                        const uint64_t* qoffsets, const int8_t* d_matrix, int32_t alpha,
+                        int32_t beta, uint32_t top_k, int32_t* d_scores, int32_t* d_top_scores,
+                        uint64_t* d_top_index, cudaStream_t stream, BatchInfo* info);

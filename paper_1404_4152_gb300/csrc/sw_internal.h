@@ -27,44 +27,80 @@ constexpr int kShortT = 8;
 constexpr int kLongT = 32;
 constexpr int kLongR = 16;
 
-// One bin of units: pairs (packed 16-bit kernels) or sequences (int32), as
-// sorted positions first_unit.. or an explicit list; plus its scratch rows.
+// One bin of units: pairs of sequences (single-query packed kernels) or
+// single sequences (batched and int32 kernels) at sorted positions
+// first_unit.., plus the bin's scratch rows.
 struct BinArgs {
     uint64_t first_unit;            // first pair (or sequence) of the bin
-    uint64_t n_units;               // pairs (PAIR kernels) or sequences (int32 kernels)
-    const uint32_t* unit_list;      // optional: explicit sorted positions (int32 rescoring)
-    const uint32_t* unit_count;     // device count for unit_list
+    uint64_t n_units;
     uint2* boundary;                // per group slot: two halves of bstride/2 entries of (H, E)
     uint64_t bstride;               // a multiple of 8
 };
 
-// Arguments of the search kernel (one launch = one query against the database).
+// Two queries searched together in the two 16-bit halves of the lanes.
+struct QueryPair {
+    uint64_t off_a, off_b;          // offsets into the concatenated queries
+    uint32_t len_a, len_b;          // len_b = 0: no second query
+    uint32_t q_a, q_b;              // output rows (q_b = UINT32_MAX: none)
+};
+
+// Arguments of the search kernel (one launch = one query, or a batch of query
+// pairs, against the database).
 struct WavefrontArgs {
     // database
     const uint8_t* tile_data;
     const uint64_t* tile_off;       // per tile byte offset into tile_data
     const uint32_t* tile_len;       // per tile padded length
     const uint32_t* sorted_ids;     // sorted position -> original index (UINT32_MAX = empty)
-    BinArgs bin[2];                 // 0: long sequences (or a rescoring list), 1: the rest
-    // query and scoring scheme
-    const uint8_t* query;
-    uint32_t qlen;
+    BinArgs bin[2];                 // 0: long sequences, 1: the rest
+    // queries and scoring scheme
+    const uint8_t* query;           // single query, or all queries concatenated
+    uint32_t qlen;                  // single query length
+    const QueryPair* pairs;         // batch: query pairs (NULL for a single query)
+    uint32_t n_pairs;
     const int8_t* matrix;
     uint32_t alphabet;
     int32_t alpha, beta;
     // outputs
-    int32_t* scores;                // original order
-    uint32_t* flag_list;            // sorted positions to rescore in int32
+    int32_t* scores;                // row q at scores + q * score_stride, original order
+    uint64_t score_stride;
+    uint2* flag_list;               // (query row, sorted position) to rescore in int32
     uint32_t* flag_count;
+    uint32_t flag_cap;
     // scheduling
     uint32_t* work_counter;
-    uint32_t* status;               // nonzero after an internal error
 };
 
 struct KernelChoice {
+    enum Mode { kPairDb = 0, kQueryPair = 1, kInt32 = 2 };
+    Mode mode;    // what the two 16-bit halves hold (or int32 lanes)
     int R;        // query rows per thread in the short bin
-    bool pair;    // two sequences per group in packed 16-bit lanes; else one in int32
 };
+
+// Arguments of the int32 rescoring kernel (a list of (query row, sorted position)).
+struct RescoreArgs {
+    const uint8_t* tile_data;
+    const uint64_t* tile_off;
+    const uint32_t* tile_len;
+    const uint32_t* sorted_ids;
+    const uint2* list;
+    const uint32_t* count;
+    uint32_t cap;
+    const uint8_t* query;           // concatenated queries
+    const uint64_t* qoff;           // per query row: offset and length (device); NULL: one
+    const uint32_t* qlen;           //   query at offset 0 of length single_qlen
+    uint32_t single_qlen;
+    const int8_t* matrix;
+    uint32_t alphabet;
+    int32_t alpha, beta;
+    int32_t* scores;
+    uint64_t score_stride;
+    uint2* boundary;                // per warp slot
+    uint64_t bstride;
+    uint32_t* work_counter;
+};
+cudaError_t launch_rescore(const RescoreArgs& a, int grid, cudaStream_t stream);
+int rescore_block_threads();
 
 // Entries past a unit's length that a boundary row half must hold (per half:
 // length + boundary_slack(), rounded up to a multiple of 4).

@@ -1,20 +1,24 @@
-// Search orchestration: one query (or a batch) against a loaded database.
+// Search orchestration: one query, or a batch, against a loaded database.
 //
-// Enqueued on one stream (the long-sequence kernel forks onto a side stream
-// and joins back), in the order of the workflow of Section III (Fig. 2):
-//   - the wavefront kernel over the long-sequence tiles (warp per pair),
-//   - the wavefront kernel over the remaining tiles (8 lanes per pair),
-//     both staging the query profile per pass (stage (i)) and aligning
-//     (stage (ii)),
-//   - int32 rescoring of any sequence whose 16-bit lanes reached the
-//     saturation threshold (exactness; the paper avoids this with 32-bit
-//     lanes, Section III),
-//   - top-k (stage (iv)).
+// Everything is enqueued on one stream in the order of the workflow of
+// Section III (Fig. 2): the persistent wavefront kernel stages the query
+// profile per pass (stage (i)) and aligns every database sequence (stage
+// (ii)); pairs whose 16-bit lanes reached the saturation threshold are
+// rescored exactly in int32 (the paper avoids this with 32-bit lanes,
+// Section III); the top-k selection replaces the full sort of stage (iv).
+//
+// A batch packs two queries into the two 16-bit halves of every lane (their
+// profile entries are then already packed), pairs queries of similar length,
+// runs all pairs in one persistent launch whose work items are (database
+// chunk, query pair), and is replayed from a captured CUDA graph when the same
+// batch shape is searched again.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <chrono>
 #include <cstring>
+#include <numeric>
+#include <vector>
 
 #include "sw.h"
 #include "sw_db.h"
@@ -29,25 +33,28 @@ constexpr int kRescoreGrid = 64;
 
 const int kShortR[] = {8, 12, 16, 20, 24};
 
-// Rows padded to whole passes times the per-step work: 4.5 ALU operations per
-// row plus about 8 per step.
-KernelChoice choose_short(uint32_t qlen, bool int32) {
-    if (int32) return KernelChoice{16, false};
+// Rows padded to whole passes times the per-step work (alu_per_row ALU
+// instructions per query row plus about 8 per step), summed over the items.
+int choose_R(const std::vector<uint32_t>& lengths, double alu_per_row) {
     int bestR = 16;
     double best = 1e300;
     for (int R : kShortR) {
         const uint32_t TR = (uint32_t)kShortT * R;
-        const double passes = (qlen + TR - 1) / TR;
-        const double cost = passes * (4.5 * R + 8.0) * (R == 16 ? 0.97 : 1.0);
+        double cost = 0;
+        for (uint32_t m : lengths) cost += (double)((m + TR - 1) / TR) * (alu_per_row * R + 8.0);
+        if (R == 16) cost *= 0.97;
         if (cost < best) { best = cost; bestR = R; }
     }
-    return KernelChoice{bestR, true};
+    return bestR;
 }
-
-KernelChoice rescore_choice() { return KernelChoice{16, false}; }
 
 bool use_int32(const sw_db* db, int32_t alpha, int32_t beta) {
     return (db->flags & SW_DB_FLAG_FORCE_INT32) || (int64_t)alpha + beta > 32768;
+}
+
+KernelChoice single_choice(uint32_t qlen, bool i32) {
+    if (i32) return KernelChoice{KernelChoice::kInt32, 16};
+    return KernelChoice{KernelChoice::kPairDb, choose_R({qlen}, 5.5)};
 }
 
 // Two halves per slot, each the longest unit plus the wavefront's slack.
@@ -62,79 +69,14 @@ int occupancy_max(const std::vector<KernelChoice>& cs) {
     return std::max(m, 1);
 }
 
-}  // namespace
-
-sw_status sw_db_prepare_search(sw_db* db) {
-    sw_status st;
-    if ((st = db_alloc(db, (void**)&db->d_counters, 256, "search counters"))) return st;
-
-    // one persistent grid for every kernel variant; scratch rows per group slot
-    std::vector<KernelChoice> all;
-    for (int R : kShortR) all.push_back(KernelChoice{R, true});
-    all.push_back(KernelChoice{16, false});
-    const int warps = wavefront_block_threads() / 32;
-    db->grid_short = db->nsm * occupancy_max(all);
-    if (db->n_long_tiles < db->n_tiles) {
-        db->bstride_short = bstride_for(db->max_len_short);
-        const uint64_t slots = (uint64_t)db->grid_short * warps * (32 / kShortT);
-        if ((st = db_alloc(db, (void**)&db->d_bnd_short, slots * db->bstride_short * sizeof(uint2),
-                           "boundary rows (short)")))
-            return st;
+std::vector<KernelChoice> all_choices() {
+    std::vector<KernelChoice> v;
+    for (int R : kShortR) {
+        v.push_back(KernelChoice{KernelChoice::kPairDb, R});
+        v.push_back(KernelChoice{KernelChoice::kQueryPair, R});
     }
-    if (db->n_long_tiles) {
-        db->bstride_long = bstride_for(db->max_len_long);
-        const uint64_t slots = (uint64_t)db->grid_short * warps * (32 / kLongT);
-        if ((st = db_alloc(db, (void**)&db->d_bnd_long, slots * db->bstride_long * sizeof(uint2),
-                           "boundary rows (long)")))
-            return st;
-    }
-    db->grid_rescore = std::min(kRescoreGrid, db->nsm * occupancy_max({rescore_choice()}));
-    db->bstride_rescore = bstride_for(std::max(4u, (db->max_len + 3u) & ~3u));
-    if ((st = db_alloc(db, (void**)&db->d_bnd_rescore,
-                       (uint64_t)db->grid_rescore * warps * (32 / kLongT) * db->bstride_rescore *
-                           sizeof(uint2),
-                       "boundary rows (rescoring)")))
-        return st;
-    db->topk_nq = 1;
-    if ((st = db_alloc(db, &db->d_topk, topk_scratch_bytes(1, SW_MAX_TOP_K, kTopkBlocks),
-                       "top-k scratch")))
-        return st;
-    topk_scratch_carve(db->d_topk, 1, SW_MAX_TOP_K, kTopkBlocks, &db->topk);
-    db->query_cap = 1u << 16;
-    if ((st = db_alloc(db, (void**)&db->d_query, db->query_cap, "query staging")) ||
-        (st = db_alloc(db, (void**)&db->d_matrix, SW_MAX_ALPHABET * SW_MAX_ALPHABET,
-                       "matrix staging")) ||
-        (st = db_alloc(db, (void**)&db->d_top_scores, SW_MAX_TOP_K * 4, "top-k scores")) ||
-        (st = db_alloc(db, (void**)&db->d_top_index, SW_MAX_TOP_K * 8, "top-k indices")))
-        return st;
-    return SW_OK;
-}
-
-namespace {
-
-WavefrontArgs base_args(sw_db* db, const uint8_t* d_query, uint32_t qlen, const int8_t* d_matrix,
-                        int32_t alpha, int32_t beta, int32_t* d_scores) {
-    WavefrontArgs a{};
-    a.tile_data = db->d_tile_data;
-    a.tile_off = db->d_tile_off;
-    a.tile_len = db->d_tile_len;
-    a.sorted_ids = db->d_sorted;
-    a.query = d_query;
-    a.qlen = qlen;
-    a.matrix = d_matrix;
-    a.alphabet = db->alphabet;
-    a.alpha = alpha;
-    a.beta = beta;
-    a.scores = d_scores;
-    a.flag_list = db->d_flags;
-    a.flag_count = db->d_counters + 3;
-    a.status = db->d_counters + 8;
-    return a;
-}
-
-int grid_for(const sw_db* db, const KernelChoice& kc, int cap) {
-    const int occ = std::max(1, wavefront_occupancy(kc, nullptr));
-    return std::max(1, std::min(cap, db->nsm * occ));
+    v.push_back(KernelChoice{KernelChoice::kInt32, 16});
+    return v;
 }
 
 cudaEvent_t take_event(sw_db* db) {
@@ -172,6 +114,67 @@ struct PhaseTimer {
 
 }  // namespace
 
+// Grow-only device buffer owned by the handle.
+sw_status ensure(sw_db* db, DevBuf& b, size_t bytes, const char* what) {
+    if (b.cap >= bytes && b.p) return SW_OK;
+    if (b.p) {
+        db_free(db, b.p, b.cap);
+        b.p = nullptr;
+        b.cap = 0;
+    }
+    size_t cap = std::max<size_t>(bytes, 256);
+    cap = (cap + 255) & ~(size_t)255;
+    void* p = nullptr;
+    cudaError_t e = db_malloc(db, &p, cap);
+    if (e != cudaSuccess) return cuda_fail(e, what);
+    b.p = p;
+    b.cap = cap;
+    return SW_OK;
+}
+
+sw_status sw_db_prepare_search(sw_db* db) {
+    sw_status st;
+    if ((st = db_alloc(db, (void**)&db->d_counters, 256, "search counters"))) return st;
+    const int warps = wavefront_block_threads() / 32;
+    db->grid_short = db->nsm * occupancy_max(all_choices());
+    if (db->n_long_tiles < db->n_tiles) {
+        db->bstride_short = bstride_for(db->max_len_short);
+        const uint64_t slots = (uint64_t)db->grid_short * warps * (32 / kShortT);
+        if ((st = db_alloc(db, (void**)&db->d_bnd_short, slots * db->bstride_short * sizeof(uint2),
+                           "boundary rows (short)")))
+            return st;
+    }
+    if (db->n_long_tiles) {
+        db->bstride_long = bstride_for(db->max_len_long);
+        const uint64_t slots = (uint64_t)db->grid_short * warps * (32 / kLongT);
+        if ((st = db_alloc(db, (void**)&db->d_bnd_long, slots * db->bstride_long * sizeof(uint2),
+                           "boundary rows (long)")))
+            return st;
+    }
+    db->grid_rescore = kRescoreGrid;
+    db->bstride_rescore = bstride_for(std::max(4u, (db->max_len + 3u) & ~3u));
+    if ((st = db_alloc(db, (void**)&db->d_bnd_rescore,
+                       (uint64_t)db->grid_rescore * (rescore_block_threads() / 32) *
+                           db->bstride_rescore * sizeof(uint2),
+                       "boundary rows (rescoring)")))
+        return st;
+    if ((st = db_alloc(db, (void**)&db->d_flags2, db->n_seqs * sizeof(uint2), "rescoring list")))
+        return st;
+    db->topk_nq = 1;
+    if ((st = db_alloc(db, &db->d_topk, topk_scratch_bytes(1, SW_MAX_TOP_K, kTopkBlocks),
+                       "top-k scratch")))
+        return st;
+    topk_scratch_carve(db->d_topk, 1, SW_MAX_TOP_K, kTopkBlocks, &db->topk);
+    db->query_cap = 1u << 16;
+    if ((st = db_alloc(db, (void**)&db->d_query, db->query_cap, "query staging")) ||
+        (st = db_alloc(db, (void**)&db->d_matrix, SW_MAX_ALPHABET * SW_MAX_ALPHABET,
+                       "matrix staging")) ||
+        (st = db_alloc(db, (void**)&db->d_top_scores, SW_MAX_TOP_K * 4, "top-k scores")) ||
+        (st = db_alloc(db, (void**)&db->d_top_index, SW_MAX_TOP_K * 8, "top-k indices")))
+        return st;
+    return SW_OK;
+}
+
 extern "C" sw_status sw_db_get_profile(sw_db* db, sw_profile* out) {
     clear_error();
     if (!db || !out) return fail(SW_ERR_INVALID_ARG, "sw_db_get_profile: NULL argument");
@@ -205,7 +208,63 @@ extern "C" sw_status sw_db_reset_profile(sw_db* db) {
     return SW_OK;
 }
 
-// Enqueue one full search on `stream`. Scores land in d_scores (original order).
+namespace {
+
+WavefrontArgs base_args(sw_db* db, const int8_t* d_matrix, int32_t alpha, int32_t beta,
+                        int32_t* d_scores, uint64_t stride, uint32_t units_per_tile) {
+    WavefrontArgs a{};
+    a.tile_data = db->d_tile_data;
+    a.tile_off = db->d_tile_off;
+    a.tile_len = db->d_tile_len;
+    a.sorted_ids = db->d_sorted;
+    a.matrix = d_matrix;
+    a.alphabet = db->alphabet;
+    a.alpha = alpha;
+    a.beta = beta;
+    a.scores = d_scores;
+    a.score_stride = stride;
+    a.bin[0].first_unit = 0;
+    a.bin[0].n_units = db->n_long_tiles * units_per_tile;
+    a.bin[0].boundary = db->d_bnd_long;
+    a.bin[0].bstride = db->bstride_long;
+    a.bin[1].first_unit = db->n_long_tiles * units_per_tile;
+    a.bin[1].n_units = (db->n_tiles - db->n_long_tiles) * units_per_tile;
+    a.bin[1].boundary = db->d_bnd_short;
+    a.bin[1].bstride = db->bstride_short;
+    a.work_counter = db->d_counters + 0;
+    a.flag_count = db->d_counters + 3;
+    return a;
+}
+
+RescoreArgs rescore_args(sw_db* db, const int8_t* d_matrix, int32_t alpha, int32_t beta,
+                         int32_t* d_scores, uint64_t stride) {
+    RescoreArgs r{};
+    r.tile_data = db->d_tile_data;
+    r.tile_off = db->d_tile_off;
+    r.tile_len = db->d_tile_len;
+    r.sorted_ids = db->d_sorted;
+    r.count = db->d_counters + 3;
+    r.matrix = d_matrix;
+    r.alphabet = db->alphabet;
+    r.alpha = alpha;
+    r.beta = beta;
+    r.scores = d_scores;
+    r.score_stride = stride;
+    r.boundary = db->d_bnd_rescore;
+    r.bstride = db->bstride_rescore;
+    r.work_counter = db->d_counters + 2;
+    return r;
+}
+
+int grid_for(const sw_db* db, const KernelChoice& kc) {
+    const int occ = std::max(1, wavefront_occupancy(kc, nullptr));
+    return std::max(1, std::min(db->grid_short, db->nsm * occ));
+}
+
+}  // namespace
+
+// Enqueue one full single-query search on `stream`. Scores land in d_scores
+// (original order).
 sw_status enqueue_search(sw_db* db, const uint8_t* d_query, uint32_t qlen, const int8_t* d_matrix,
                          int32_t alpha, int32_t beta, uint32_t top_k, int32_t* d_scores,
                          int32_t* d_top_scores, uint64_t* d_top_index, cudaStream_t stream) {
@@ -213,35 +272,28 @@ sw_status enqueue_search(sw_db* db, const uint8_t* d_query, uint32_t qlen, const
     const bool i32 = use_int32(db, alpha, beta);
     if ((e = cudaMemsetAsync(db->d_counters, 0, 64, stream)) != cudaSuccess)
         return cuda_fail(e, "search: counter reset");
-    const uint64_t per_tile = i32 ? kTileSeqs : kTilePairs;  // units per tile
+    const KernelChoice kc = single_choice(qlen, i32);
     {
-        WavefrontArgs a = base_args(db, d_query, qlen, d_matrix, alpha, beta, d_scores);
-        const KernelChoice kc = choose_short(qlen, i32);
-        a.bin[0].first_unit = 0;
-        a.bin[0].n_units = db->n_long_tiles * per_tile;
-        a.bin[0].boundary = db->d_bnd_long;
-        a.bin[0].bstride = db->bstride_long;
-        a.bin[1].first_unit = db->n_long_tiles * per_tile;
-        a.bin[1].n_units = (db->n_tiles - db->n_long_tiles) * per_tile;
-        a.bin[1].boundary = db->d_bnd_short;
-        a.bin[1].bstride = db->bstride_short;
-        a.work_counter = db->d_counters + 0;
+        WavefrontArgs a = base_args(db, d_matrix, alpha, beta, d_scores, db->n_seqs,
+                                    kc.mode == KernelChoice::kPairDb ? kTilePairs : kTileSeqs);
+        a.query = d_query;
+        a.qlen = qlen;
+        a.flag_list = db->d_flags2;
+        a.flag_cap = (uint32_t)std::min<uint64_t>(db->n_seqs, 0xffffffffu);
         PhaseTimer pt(db, 0, stream, (uint64_t)qlen * db->total_residues);
-        if ((e = launch_wavefront(kc, a, grid_for(db, kc, db->grid_short), stream)) != cudaSuccess)
+        if ((e = launch_wavefront(kc, a, grid_for(db, kc), stream)) != cudaSuccess)
             return cuda_fail(e, "search: wavefront kernel");
         pt.done();
         db->launches += 1;
     }
     if (!i32) {
-        WavefrontArgs a = base_args(db, d_query, qlen, d_matrix, alpha, beta, d_scores);
-        a.bin[0].unit_list = db->d_flags;
-        a.bin[0].unit_count = db->d_counters + 3;
-        a.bin[0].boundary = db->d_bnd_rescore;
-        a.bin[0].bstride = db->bstride_rescore;
-        a.bin[1].n_units = 0;
-        a.work_counter = db->d_counters + 2;
+        RescoreArgs r = rescore_args(db, d_matrix, alpha, beta, d_scores, db->n_seqs);
+        r.list = db->d_flags2;
+        r.cap = (uint32_t)std::min<uint64_t>(db->n_seqs, 0xffffffffu);
+        r.query = d_query;
+        r.single_qlen = qlen;
         PhaseTimer pt(db, 1, stream, 0);
-        if ((e = launch_wavefront(rescore_choice(), a, db->grid_rescore, stream)) != cudaSuccess)
+        if ((e = launch_rescore(r, db->grid_rescore, stream)) != cudaSuccess)
             return cuda_fail(e, "search: int32 rescoring kernel");
         pt.done();
         db->launches += 1;
@@ -254,6 +306,198 @@ sw_status enqueue_search(sw_db* db, const uint8_t* d_query, uint32_t qlen, const
         pt.done();
         db->launches += topk_launch_count();
     }
+    return SW_OK;
+}
+
+// ---------------------------------------------------------------------------
+// batches
+// ---------------------------------------------------------------------------
+
+namespace {
+
+struct BatchPlan {
+    std::vector<QueryPair> pairs;
+    std::vector<uint64_t> qoff;
+    std::vector<uint32_t> qlen;
+    KernelChoice kc{KernelChoice::kQueryPair, 16};
+    uint64_t cells = 0;
+    uint32_t flag_cap = 0;
+};
+
+// Pair queries of similar length (longest first) and pick the kernel shape.
+BatchPlan plan_batch(const sw_db* db, uint32_t nq, const uint64_t* qoffsets) {
+    BatchPlan pl;
+    pl.qoff.assign(qoffsets, qoffsets + nq);
+    pl.qlen.resize(nq);
+    for (uint32_t q = 0; q < nq; ++q) pl.qlen[q] = (uint32_t)(qoffsets[q + 1] - qoffsets[q]);
+    std::vector<uint32_t> order(nq);
+    std::iota(order.begin(), order.end(), 0u);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](uint32_t x, uint32_t y) { return pl.qlen[x] > pl.qlen[y]; });
+    std::vector<uint32_t> item_len;
+    for (uint32_t i = 0; i < nq; i += 2) {
+        QueryPair p{};
+        const uint32_t qa = order[i];
+        p.off_a = pl.qoff[qa];
+        p.len_a = pl.qlen[qa];
+        p.q_a = qa;
+        if (i + 1 < nq) {
+            const uint32_t qb = order[i + 1];
+            p.off_b = pl.qoff[qb];
+            p.len_b = pl.qlen[qb];
+            p.q_b = qb;
+        } else {
+            p.off_b = p.off_a;
+            p.len_b = 0;
+            p.q_b = 0xffffffffu;
+        }
+        pl.pairs.push_back(p);
+        item_len.push_back(std::max(p.len_a, p.len_b));
+    }
+    pl.kc = KernelChoice{KernelChoice::kQueryPair, choose_R(item_len, 4.5)};
+    for (uint32_t q = 0; q < nq; ++q) pl.cells += (uint64_t)pl.qlen[q] * db->total_residues;
+    pl.flag_cap = (uint32_t)std::min<uint64_t>(std::max<uint64_t>(db->n_seqs, 1u << 20), 1u << 26);
+    return pl;
+}
+
+sw_status upload_plan(sw_db* db, const BatchPlan& pl, cudaStream_t stream) {
+    sw_status st;
+    const size_t np = pl.pairs.size(), nq = pl.qlen.size();
+    if ((st = ensure(db, db->b_pairs, np * sizeof(QueryPair), "batch pairs")) ||
+        (st = ensure(db, db->b_qoff, nq * 8, "batch query offsets")) ||
+        (st = ensure(db, db->b_qlen, nq * 4, "batch query lengths")) ||
+        (st = ensure(db, db->b_flags, (size_t)pl.flag_cap * sizeof(uint2), "batch rescoring list")) ||
+        (st = ensure(db, db->b_topk, topk_scratch_bytes((uint32_t)nq, SW_MAX_TOP_K, kTopkBlocks),
+                     "batch top-k scratch")))
+        return st;
+    cudaError_t e;
+    // pageable sources: each copy has consumed its host data when the call returns
+    if ((e = cudaMemcpyAsync(db->b_pairs.p, pl.pairs.data(), np * sizeof(QueryPair),
+                             cudaMemcpyHostToDevice, stream)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(db->b_qoff.p, pl.qoff.data(), nq * 8, cudaMemcpyHostToDevice,
+                             stream)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(db->b_qlen.p, pl.qlen.data(), nq * 4, cudaMemcpyHostToDevice,
+                             stream)) != cudaSuccess)
+        return cuda_fail(e, "batch: plan upload");
+    return SW_OK;
+}
+
+// The kernels of one batch (capturable: memsets and launches only).
+sw_status launch_batch(sw_db* db, const BatchPlan& pl, const uint8_t* d_queries,
+                       const int8_t* d_matrix, int32_t alpha, int32_t beta, uint32_t top_k,
+                       int32_t* d_scores, int32_t* d_top_scores, uint64_t* d_top_index,
+                       cudaStream_t stream) {
+    cudaError_t e;
+    const uint32_t nq = (uint32_t)pl.qlen.size();
+    if ((e = cudaMemsetAsync(db->d_counters, 0, 64, stream)) != cudaSuccess)
+        return cuda_fail(e, "batch: counter reset");
+    WavefrontArgs a = base_args(db, d_matrix, alpha, beta, d_scores, db->n_seqs, kTileSeqs);
+    a.query = d_queries;
+    a.pairs = (const QueryPair*)db->b_pairs.p;
+    a.n_pairs = (uint32_t)pl.pairs.size();
+    a.flag_list = (uint2*)db->b_flags.p;
+    a.flag_cap = pl.flag_cap;
+    if ((e = launch_wavefront(pl.kc, a, grid_for(db, pl.kc), stream)) != cudaSuccess)
+        return cuda_fail(e, "batch: wavefront kernel");
+    RescoreArgs r = rescore_args(db, d_matrix, alpha, beta, d_scores, db->n_seqs);
+    r.list = (const uint2*)db->b_flags.p;
+    r.cap = pl.flag_cap;
+    r.query = d_queries;
+    r.qoff = (const uint64_t*)db->b_qoff.p;
+    r.qlen = (const uint32_t*)db->b_qlen.p;
+    if ((e = launch_rescore(r, db->grid_rescore, stream)) != cudaSuccess)
+        return cuda_fail(e, "batch: int32 rescoring kernel");
+    if (top_k) {
+        TopkScratch ts;
+        topk_scratch_carve(db->b_topk.p, nq, SW_MAX_TOP_K, kTopkBlocks, &ts);
+        if ((e = launch_topk(d_scores, db->n_seqs, db->n_seqs, nq, top_k, ts, d_top_scores,
+                             d_top_index, stream)) != cudaSuccess)
+            return cuda_fail(e, "batch: top-k");
+    }
+    return SW_OK;
+}
+
+// Graph replay key: everything a captured batch bakes in.
+bool same_key(const BatchGraph& g, const BatchPlan& pl, const void* q, const void* m,
+              int32_t alpha, int32_t beta, uint32_t k, const void* s, const void* ts,
+              const void* ti, cudaStream_t st) {
+    return g.exec && g.queries == q && g.matrix == m && g.alpha == alpha && g.beta == beta &&
+           g.top_k == k && g.scores == s && g.top_s == ts && g.top_i == ti && g.stream == st &&
+           g.qoff == pl.qoff && g.qlen == pl.qlen;
+}
+
+}  // namespace
+
+// Enqueue a batch on `stream`, replaying the captured graph when the batch
+// shape and buffers match the previous call.
+sw_status enqueue_batch(sw_db* db, uint32_t nq, const uint8_t* d_queries,
+                        const uint64_t* qoffsets, const int8_t* d_matrix, int32_t alpha,
+                        int32_t beta, uint32_t top_k, int32_t* d_scores, int32_t* d_top_scores,
+                        uint64_t* d_top_index, cudaStream_t stream, BatchInfo* info) {
+    if (use_int32(db, alpha, beta)) {
+        // wide penalties or forced int32: one int32 search per query
+        for (uint32_t q = 0; q < nq; ++q) {
+            sw_status st = enqueue_search(
+                db, d_queries + qoffsets[q], (uint32_t)(qoffsets[q + 1] - qoffsets[q]), d_matrix,
+                alpha, beta, top_k, d_scores + (uint64_t)q * db->n_seqs,
+                top_k ? d_top_scores + (uint64_t)q * top_k : nullptr,
+                top_k ? d_top_index + (uint64_t)q * top_k : nullptr, stream);
+            if (st) return st;
+        }
+        if (info) info->flag_cap = 0;
+        return SW_OK;
+    }
+    BatchPlan pl = plan_batch(db, nq, qoffsets);
+    sw_status st = upload_plan(db, pl, stream);
+    if (st) return st;
+    if (info) {
+        info->cells = pl.cells;
+        info->flag_cap = pl.flag_cap;
+    }
+    cudaError_t e;
+    BatchGraph& g = db->graph;
+    const bool hit = same_key(g, pl, d_queries, d_matrix, alpha, beta, top_k, d_scores,
+                              d_top_scores, d_top_index, stream);
+    if (!hit) {
+        if (g.exec) {
+            cudaGraphExecDestroy(g.exec);
+            g.exec = nullptr;
+        }
+        cudaGraph_t graph = nullptr;
+        if ((e = cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+            return cuda_fail(e, "batch: begin capture");
+        st = launch_batch(db, pl, d_queries, d_matrix, alpha, beta, top_k, d_scores, d_top_scores,
+                          d_top_index, stream);
+        e = cudaStreamEndCapture(stream, &graph);
+        if (st) {
+            if (graph) cudaGraphDestroy(graph);
+            return st;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "batch: end capture");
+        e = cudaGraphInstantiate(&g.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            g.exec = nullptr;
+            return cuda_fail(e, "batch: graph instantiation");
+        }
+        g.queries = d_queries;
+        g.matrix = d_matrix;
+        g.alpha = alpha;
+        g.beta = beta;
+        g.top_k = top_k;
+        g.scores = d_scores;
+        g.top_s = d_top_scores;
+        g.top_i = d_top_index;
+        g.stream = stream;
+        g.qoff = pl.qoff;
+        g.qlen = pl.qlen;
+        g.kernels = 2 + (top_k ? topk_launch_count() : 0);
+    }
+    PhaseTimer pt(db, 3, stream, pl.cells);
+    if ((e = cudaGraphLaunch(g.exec, stream)) != cudaSuccess)
+        return cuda_fail(e, "batch: graph launch");
+    pt.done();
+    db->launches += g.kernels;
     return SW_OK;
 }
 
@@ -312,6 +556,19 @@ sw_status validate_host_query(const sw_db* db, const uint8_t* query, uint32_t ql
     return SW_OK;
 }
 
+sw_status check_batch(const sw_db* db, uint32_t nq, const uint64_t* qoffsets, int32_t alpha,
+                      int32_t beta, uint32_t top_k, const char* fn) {
+    if (!db) return fail(SW_ERR_INVALID_ARG, "%s: db is NULL", fn);
+    if (!qoffsets) return fail(SW_ERR_INVALID_ARG, "%s: NULL query offsets", fn);
+    for (uint32_t q = 0; q < nq; ++q) {
+        if (qoffsets[q + 1] <= qoffsets[q])
+            return fail(SW_ERR_INVALID_ARG, "%s: query %u is empty or offsets not ascending", fn, q);
+        if (qoffsets[q + 1] - qoffsets[q] > 0x7fffffffull)
+            return fail(SW_ERR_INVALID_ARG, "%s: query %u is too long", fn, q);
+    }
+    return check_common(db, 1, alpha, beta, top_k, fn);
+}
+
 }  // namespace
 
 extern "C" sw_status sw_search(sw_db* db, const uint8_t* query, uint32_t qlen,
@@ -329,10 +586,8 @@ extern "C" sw_status sw_search(sw_db* db, const uint8_t* query, uint32_t qlen,
     if ((st = stage_query(db, query, qlen, matrix))) return st;
     cudaError_t e;
     cudaEventRecord(db->ev_t0, db->stream);
-    int32_t* d_ts = db->d_top_scores;
-    uint64_t* d_ti = db->d_top_index;
-    st = enqueue_search(db, db->d_query, qlen, db->d_matrix, alpha, beta, top_k, db->d_scores, d_ts,
-                        d_ti, db->stream);
+    st = enqueue_search(db, db->d_query, qlen, db->d_matrix, alpha, beta, top_k, db->d_scores,
+                        db->d_top_scores, db->d_top_index, db->stream);
     if (st) return st;
     cudaEventRecord(db->ev_t1, db->stream);
     const uint32_t kk = (uint32_t)std::min<uint64_t>(top_k, db->n_seqs);
@@ -341,9 +596,11 @@ extern "C" sw_status sw_search(sw_db* db, const uint8_t* query, uint32_t qlen,
         e = cudaMemcpyAsync(scores, db->d_scores, db->n_seqs * 4, cudaMemcpyDeviceToHost,
                             db->stream);
     if (e == cudaSuccess && kk)
-        e = cudaMemcpyAsync(top_scores, d_ts, kk * 4, cudaMemcpyDeviceToHost, db->stream);
+        e = cudaMemcpyAsync(top_scores, db->d_top_scores, kk * 4, cudaMemcpyDeviceToHost,
+                            db->stream);
     if (e == cudaSuccess && kk)
-        e = cudaMemcpyAsync(top_index, d_ti, kk * 8, cudaMemcpyDeviceToHost, db->stream);
+        e = cudaMemcpyAsync(top_index, db->d_top_index, kk * 8, cudaMemcpyDeviceToHost,
+                            db->stream);
     uint32_t nflag = 0;
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(&nflag, db->d_counters + 3, 4, cudaMemcpyDeviceToHost, db->stream);
@@ -380,29 +637,115 @@ extern "C" sw_status sw_search_device(sw_db* db, const uint8_t* d_query, uint32_
                           (cudaStream_t)stream);
 }
 
+extern "C" sw_status sw_search_batch_device(sw_db* db, uint32_t nq, const uint8_t* d_queries,
+                                            const uint64_t* qoffsets, const int8_t* d_matrix,
+                                            int32_t alpha, int32_t beta, uint32_t top_k,
+                                            int32_t* d_scores, int32_t* d_top_scores,
+                                            uint64_t* d_top_index, void* stream) {
+    clear_error();
+    sw_status st;
+    if ((st = check_batch(db, nq, qoffsets, alpha, beta, top_k, "sw_search_batch_device")))
+        return st;
+    if (nq == 0) return SW_OK;
+    if (!d_queries || !d_matrix || !d_scores)
+        return fail(SW_ERR_INVALID_ARG, "sw_search_batch_device: NULL device buffer");
+    if (top_k && (!d_top_scores || !d_top_index))
+        return fail(SW_ERR_INVALID_ARG, "sw_search_batch_device: top_k > 0 needs output buffers");
+    DeviceScope scope(db->device);
+    return enqueue_batch(db, nq, d_queries, qoffsets, d_matrix, alpha, beta, top_k, d_scores,
+                         d_top_scores, d_top_index, (cudaStream_t)stream, nullptr);
+}
+
 extern "C" sw_status sw_search_batch(sw_db* db, uint32_t nq, const uint8_t* const* queries,
                                      const uint32_t* qlens, const int8_t* matrix, int32_t alpha,
                                      int32_t beta, uint32_t top_k, int32_t* const* scores,
                                      int32_t* top_scores, uint64_t* top_index, uint32_t* n_top,
                                      sw_stats* stats) {
     clear_error();
+    const auto t0 = std::chrono::steady_clock::now();
     if (!db) return fail(SW_ERR_INVALID_ARG, "sw_search_batch: db is NULL");
     if (nq == 0) return SW_OK;
-    if (!queries || !qlens) return fail(SW_ERR_INVALID_ARG, "sw_search_batch: NULL queries");
-    sw_stats total{};
+    if (!queries || !qlens || !matrix)
+        return fail(SW_ERR_INVALID_ARG, "sw_search_batch: NULL queries, lengths or matrix");
+    if (top_k && (!top_scores || !top_index))
+        return fail(SW_ERR_INVALID_ARG, "sw_search_batch: top_k > 0 needs top_scores and top_index");
+    std::vector<uint64_t> off(nq + 1, 0);
     for (uint32_t q = 0; q < nq; ++q) {
-        sw_stats s{};
-        sw_status st = sw_search(db, queries[q], qlens[q], matrix, alpha, beta, top_k,
-                                 scores ? scores[q] : nullptr,
-                                 top_scores ? top_scores + (size_t)q * top_k : nullptr,
-                                 top_index ? top_index + (size_t)q * top_k : nullptr,
-                                 n_top ? n_top + q : nullptr, &s);
-        if (st) return st;
-        total.cells += s.cells;
-        total.recomputed += s.recomputed;
-        total.kernel_ms += s.kernel_ms;
-        total.total_ms += s.total_ms;
+        sw_status st;
+        if ((st = check_common(db, qlens[q], alpha, beta, top_k, "sw_search_batch"))) return st;
+        if ((st = validate_host_query(db, queries[q], qlens[q], matrix, "sw_search_batch")))
+            return st;
+        off[q + 1] = off[q] + qlens[q];
     }
-    if (stats) *stats = total;
+    DeviceScope scope(db->device);
+    sw_status st;
+    const size_t kk1 = std::max(top_k, 1u);
+    if ((st = ensure(db, db->b_queries, off[nq], "batch queries")) ||
+        (st = ensure(db, db->b_scores, (size_t)nq * db->n_seqs * 4, "batch scores")) ||
+        (st = ensure(db, db->b_top, (size_t)nq * kk1 * 16, "batch top-k")))
+        return st;
+    cudaError_t e;
+    for (uint32_t q = 0; q < nq; ++q)
+        if ((e = cudaMemcpyAsync((uint8_t*)db->b_queries.p + off[q], queries[q], qlens[q],
+                                 cudaMemcpyHostToDevice, db->stream)) != cudaSuccess)
+            return cuda_fail(e, "sw_search_batch: query upload");
+    if ((e = cudaMemcpyAsync(db->d_matrix, matrix, (size_t)db->alphabet * db->alphabet,
+                             cudaMemcpyHostToDevice, db->stream)) != cudaSuccess)
+        return cuda_fail(e, "sw_search_batch: matrix upload");
+    uint64_t* d_ti = (uint64_t*)db->b_top.p;
+    int32_t* d_ts = (int32_t*)((char*)db->b_top.p + (size_t)nq * kk1 * 8);
+    BatchInfo info{};
+    cudaEventRecord(db->ev_t0, db->stream);
+    if ((st = enqueue_batch(db, nq, (const uint8_t*)db->b_queries.p, off.data(), db->d_matrix,
+                            alpha, beta, top_k, (int32_t*)db->b_scores.p, d_ts, d_ti, db->stream,
+                            &info)))
+        return st;
+    cudaEventRecord(db->ev_t1, db->stream);
+    uint32_t nflag = 0;
+    if ((e = cudaMemcpyAsync(&nflag, db->d_counters + 3, 4, cudaMemcpyDeviceToHost, db->stream)) !=
+            cudaSuccess ||
+        (e = cudaStreamSynchronize(db->stream)) != cudaSuccess)
+        return cuda_fail(e, "sw_search_batch");
+    if (info.flag_cap && nflag > info.flag_cap) {
+        // more saturated pairs than the rescoring list holds: search again in int32
+        const uint32_t keep = db->flags;
+        db->flags |= SW_DB_FLAG_FORCE_INT32;
+        st = enqueue_batch(db, nq, (const uint8_t*)db->b_queries.p, off.data(), db->d_matrix,
+                           alpha, beta, top_k, (int32_t*)db->b_scores.p, d_ts, d_ti, db->stream,
+                           nullptr);
+        db->flags = keep;
+        if (st) return st;
+        if ((e = cudaStreamSynchronize(db->stream)) != cudaSuccess)
+            return cuda_fail(e, "sw_search_batch: int32 retry");
+    }
+    const uint32_t kk = (uint32_t)std::min<uint64_t>(top_k, db->n_seqs);
+    e = cudaSuccess;
+    for (uint32_t q = 0; q < nq && e == cudaSuccess; ++q) {
+        if (scores && scores[q])
+            e = cudaMemcpyAsync(scores[q], (int32_t*)db->b_scores.p + (size_t)q * db->n_seqs,
+                                db->n_seqs * 4, cudaMemcpyDeviceToHost, db->stream);
+        if (e == cudaSuccess && kk) {
+            e = cudaMemcpyAsync(top_scores + (size_t)q * top_k, d_ts + (size_t)q * top_k, kk * 4,
+                                cudaMemcpyDeviceToHost, db->stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(top_index + (size_t)q * top_k, d_ti + (size_t)q * top_k,
+                                    kk * 8, cudaMemcpyDeviceToHost, db->stream);
+        }
+        if (n_top) n_top[q] = kk;
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(db->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "sw_search_batch: copy out");
+    if (stats) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, db->ev_t0, db->ev_t1);
+        uint64_t cells = 0;
+        for (uint32_t q = 0; q < nq; ++q) cells += (uint64_t)qlens[q] * db->total_residues;
+        stats->cells = cells;
+        stats->recomputed = nflag;
+        stats->kernel_ms = ms;
+        stats->total_ms =
+            std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0)
+                .count();
+    }
     return SW_OK;
 }

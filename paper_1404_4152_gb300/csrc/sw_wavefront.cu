@@ -2,10 +2,12 @@
 // affine gaps): the hot loop of a database search.
 //
 // Design (GB300-first; the paper's Xeon Phi kernels are prior art):
-//  - A group of T consecutive lanes cooperates on one database "unit": a pair
-//    of length-sorted sequences held in the two 16-bit halves of every
-//    register (packed s16x2 arithmetic, the inter-sequence model of Section
-//    III.B with two lanes per register), or one sequence in int32.
+//  - A group of T consecutive lanes cooperates on one unit of work: two
+//    alignments held in the two 16-bit halves of every register (packed
+//    s16x2 arithmetic, the inter-sequence model of Section III.B with two
+//    lanes per register), or one alignment in int32. The two alignments are
+//    either one query against two length-sorted database sequences (a single
+//    search) or two queries against one database sequence (a batch).
 //  - Each thread holds R query rows (H and F of its rows live in registers,
 //    the linear-space rows of Section III.A). The database sequence streams
 //    through the group one column per step; thread t works on column s - t at
@@ -16,24 +18,31 @@
 //    global scratch row (the paper's tiled computation, Section IV.C; two
 //    halves per group, read one / write the other) and the block stages the
 //    next T*R rows of the query profile (Section III.B.2) in shared memory.
-//  - The integer ALU pipe is the bottleneck (every max, fused add-max and
-//    byte permute runs there; plain 16x2 adds run on the FMA pipe), so the
-//    cell update is written to keep ALU work at 4.5 instructions per cell
-//    pair: unpack the two int8 scores (prmt), H = max3(diag + s, E, F, 0)
-//    with the add on the FMA pipe, E and F as fused add-max, and the running
-//    maximum fused two rows at a time.
+//  - The integer ALU pipe is the bottleneck: every max, fused add-max and
+//    byte permute runs there (16x2 adds run on the FMA pipe). One cell pair
+//    costs 4.5 ALU instructions (three fused add-max, one max, half of a
+//    three-way running max) plus, for two database sequences, one permute
+//    that merges their two int8 scores; two queries share the database
+//    residue, so their profile entry is already the packed pair.
+//  - The running maximum tracks x = H[i-1][j-1] + fsbt instead of H: E and F
+//    only carry values strictly below an earlier H (by beta, or as a chain of
+//    equal values ending at one), so the largest H of the matrix is
+//    max(0, largest x). That keeps x live on the FMA pipe and leaves H a
+//    single three-way max with the zero floor.
 //  - Exactness: 16-bit lanes wrap, so a lane whose maximum reaches
-//    thr16 = 32767 - max(0, max fsbt) is flagged and rescored by the int32
-//    kernel. Below that threshold no intermediate can leave the 16-bit range
+//    thr16 = 32767 - max(0, max fsbt) is flagged and rescored in int32.
+//    Below that threshold no intermediate can leave the 16-bit range
 //    (H <= thr16 bounds H + fsbt; E, F >= -beta because H >= 0; E - alpha and
 //    F - alpha >= -(alpha + beta) >= -32768 is required of the 16-bit path),
-//    and the first cell that exceeds it is computed exactly, so the running
-//    maximum of a lane that ever exceeded thr16 ends at or above it.
+//    and the first cell whose H exceeds it does so through x (its E and F are
+//    at most thr16 - beta), which is computed exactly, so the running maximum
+//    of a lane that ever exceeded thr16 ends above it.
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <type_traits>
 
 #include "sw_internal.h"
+#include "sw_lanes.cuh"
 
 namespace swgb {
 
@@ -42,80 +51,13 @@ namespace {
 constexpr int kWarps = 8;
 constexpr int kThreads = kWarps * 32;
 
-__device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
-    uint32_t d;
-    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(sel));
-    return d;
-}
-// Packed pair of 16-bit lanes: low half = first sequence, high half = second.
-struct LaneS16x2 {
-    using V = uint32_t;
-    static __device__ __forceinline__ V splat(int x) {
-        const uint32_t u = (uint16_t)(int16_t)x;
-        return u | (u << 16);
-    }
-    static __device__ __forceinline__ V vmax(V a, V b) {
-        V d;
-        asm("max.s16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
-        return d;
-    }
-    static __device__ __forceinline__ V vadd(V a, V b) {
-        V d;
-        asm("add.s16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
-        return d;
-    }
-    // max(a + b, c, 0) per lane
-    static __device__ __forceinline__ V addmax_relu(V a, V b, V c) {
-        return __viaddmax_s16x2_relu(a, b, c);
-    }
-    // max(a + b, c) per lane
-    static __device__ __forceinline__ V addmax(V a, V b, V c) { return __viaddmax_s16x2(a, b, c); }
-    // max(a, b, c, 0) per lane
-    static __device__ __forceinline__ V max3_relu(V a, V b, V c) { return __vimax3_s16x2_relu(a, b, c); }
-};
-
-// One sequence in a 32-bit lane.
-struct LaneS32 {
-    using V = int32_t;
-    static __device__ __forceinline__ V splat(int x) { return x; }
-    static __device__ __forceinline__ V vmax(V a, V b) { return max(a, b); }
-    static __device__ __forceinline__ V vadd(V a, V b) { return a + b; }
-    static __device__ __forceinline__ V addmax_relu(V a, V b, V c) {
-        return __viaddmax_s32_relu(a, b, c);
-    }
-    static __device__ __forceinline__ V addmax(V a, V b, V c) { return __viaddmax_s32(a, b, c); }
-    static __device__ __forceinline__ V max3_relu(V a, V b, V c) { return __vimax3_s32_relu(a, b, c); }
-};
-
 // fsbt(q[row], r) for one query row, 0 outside the query or the alphabet.
-__device__ __forceinline__ int profile_score(const WavefrontArgs& a, uint32_t row, uint32_t r) {
-    if (row >= a.qlen || r >= a.alphabet) return 0;
-    const uint32_t qc = a.query[row];
-    return qc < a.alphabet ? (int)a.matrix[qc * a.alphabet + r] : 0;
+__device__ __forceinline__ int profile_score(const uint8_t* q, uint32_t qlen, const int8_t* matrix,
+                                             uint32_t A, uint32_t row, uint32_t r) {
+    if (row >= qlen || r >= A) return 0;
+    const uint32_t qc = q[row];
+    return qc < A ? (int)matrix[qc * A + r] : 0;
 }
-
-// Query profile of one pass in shared memory: prof[r][k] = fsbt(q[p*T*R + k], r)
-// as int8, r = 0..32 (32 = pad code, all zero). Thread t reads its R rows for
-// one code as R contiguous bytes at r * T*R + t * R.
-template <int T, int R, bool PAIR>
-struct Profile {
-    static constexpr int TR = T * R;
-    static constexpr size_t kBytes = (size_t)kProfileRows * TR;
-
-    static __device__ __forceinline__ void stage(uint8_t* prof, const WavefrontArgs& a, uint32_t p) {
-        for (uint32_t idx = threadIdx.x; idx < kProfileRows * (TR / 4); idx += kThreads) {
-            const uint32_t r = idx / (TR / 4);
-            const uint32_t k4 = (idx % (TR / 4)) * 4;
-            uint32_t word = 0;
-#pragma unroll
-            for (int b = 0; b < 4; ++b) {
-                const int v = profile_score(a, p * TR + k4 + b, r);
-                word |= ((uint32_t)(uint8_t)(int8_t)v) << (8 * b);
-            }
-            reinterpret_cast<uint32_t*>(prof)[idx] = word;
-        }
-    }
-};
 
 template <int R>
 __device__ __forceinline__ void load_rows(const uint8_t* p, uint32_t (&w)[R / 4]) {
@@ -137,53 +79,170 @@ __device__ __forceinline__ void load_rows(const uint8_t* p, uint32_t (&w)[R / 4]
     }
 }
 
-// Substitution scores of one column for a thread's R rows, as lane words.
-template <int T, int R, bool PAIR>
-struct ColumnScores {
-    using Lane = typename std::conditional<PAIR, LaneS16x2, LaneS32>::type;
-    using V = typename Lane::V;
-    uint32_t wa[R / 4], wb[PAIR ? R / 4 : 1];
+__device__ __forceinline__ uint32_t word_of(const uint4& v, int i) {
+    return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
+}
 
-    __device__ __forceinline__ void load(const uint8_t* prof, uint32_t ca, uint32_t cb, int t) {
-        const uint8_t* my_rows = prof + t * R;
-        load_rows<R>(my_rows + ca * (T * R), wa);
-        if (PAIR) load_rows<R>(my_rows + cb * (T * R), reinterpret_cast<uint32_t(&)[R / 4]>(wb));
-    }
-    // row l: both sequences' int8 scores sign-extended into the two 16-bit
-    // lanes (pair), or the int32 score
-    __device__ __forceinline__ V row(int l) const {
-        const uint32_t b = (uint32_t)(l & 3);
-        if (PAIR) {
-            return prmt(wa[l / 4], wb[l / 4], b | ((8u | b) << 4) | ((4u + b) << 8) | ((12u + b) << 12));
-        } else {
-            const uint32_t x = 8u | b;
-            return (V)prmt(wa[l / 4], 0u, b | (x << 4) | (x << 8) | (x << 12));
+// The query (or query pair) of one work item.
+struct ItemQuery {
+    const uint8_t* qa;
+    const uint8_t* qb;
+    uint32_t la, lb;  // lengths (lb = 0 when there is no second query)
+    uint32_t ia, ib;  // output rows of the two queries (ib = UINT32_MAX: none)
+};
+
+// ---------------------------------------------------------------------------
+// Modes: what the two halves of a lane hold, how the profile is laid out, and
+// where results go.
+// ---------------------------------------------------------------------------
+
+// One query, two database sequences per group (16-bit halves = sequences).
+// Profile: int8 prof[r][k] = fsbt(q[p*T*R + k], r); thread t reads R contiguous
+// bytes at r * T*R + t * R; a permute merges the two sequences' scores.
+struct ModePairDb {
+    using Lane = LaneS16x2;
+    static constexpr bool kPairStream = true;  // both sequences of the tile pair
+    template <int T, int R>
+    struct Prof {
+        static constexpr int TR = T * R;
+        static constexpr size_t kBytes = (size_t)kProfileRows * TR;
+        static __device__ __forceinline__ void stage(uint8_t* prof, const ItemQuery& iq,
+                                                     const WavefrontArgs& a, uint32_t p) {
+            for (uint32_t idx = threadIdx.x; idx < kProfileRows * (TR / 4); idx += kThreads) {
+                const uint32_t r = idx / (TR / 4);
+                const uint32_t k4 = (idx % (TR / 4)) * 4;
+                uint32_t word = 0;
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    const int v = profile_score(iq.qa, iq.la, a.matrix, a.alphabet, p * TR + k4 + b, r);
+                    word |= ((uint32_t)(uint8_t)(int8_t)v) << (8 * b);
+                }
+                reinterpret_cast<uint32_t*>(prof)[idx] = word;
+            }
         }
-    }
+    };
+    template <int T, int R>
+    struct Cols {
+        uint32_t wa[R / 4], wb[R / 4];
+        __device__ __forceinline__ void load(const uint8_t* prof, uint32_t code, int t) {
+            const uint8_t* my = prof + t * R;
+            load_rows<R>(my + (code & 0xffu) * (T * R), wa);
+            load_rows<R>(my + (code >> 8) * (T * R), wb);
+        }
+        __device__ __forceinline__ uint32_t row(int l) const {
+            const uint32_t b = (uint32_t)(l & 3);
+            return prmt(wa[l / 4], wb[l / 4], b | ((8u | b) << 4) | ((4u + b) << 8) | ((12u + b) << 12));
+        }
+    };
+};
+
+// 32-bit profile words in 4-row chunks laid out [r][R/4][T][4 words]: thread t
+// reads chunk c of code r at ((r * R/4 + c) * T + t) * 16, so the 8 lanes of a
+// quarter-warp hit 8 different 16-byte bank groups whatever codes they use.
+template <int T, int R>
+__device__ __forceinline__ void load_chunks(const uint8_t* prof, uint32_t code, int t,
+                                            uint4 (&w)[R / 4]) {
+    const uint4* p = reinterpret_cast<const uint4*>(prof) + (size_t)code * (R / 4) * T + t;
+#pragma unroll
+    for (int c = 0; c < R / 4; ++c) w[c] = p[c * T];
+}
+
+// Two queries, one database sequence per group (16-bit halves = queries).
+// Profile words hold both queries' scores for one (row, code).
+struct ModeQueryPair {
+    using Lane = LaneS16x2;
+    static constexpr bool kPairStream = false;
+    template <int T, int R>
+    struct Prof {
+        static constexpr int TR = T * R;
+        static constexpr size_t kBytes = (size_t)kProfileRows * TR * 4;
+        static __device__ __forceinline__ void stage(uint8_t* prof, const ItemQuery& iq,
+                                                     const WavefrontArgs& a, uint32_t p) {
+            for (uint32_t idx = threadIdx.x; idx < kProfileRows * (TR / 4); idx += kThreads) {
+                const uint32_t r = idx / (TR / 4), rem = idx % (TR / 4);
+                const uint32_t c = rem / T, t = rem % T;
+                const uint32_t row0 = p * TR + t * R + c * 4;
+                uint32_t v[4];
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    const uint32_t lo = (uint16_t)(int16_t)profile_score(iq.qa, iq.la, a.matrix,
+                                                                         a.alphabet, row0 + b, r);
+                    const uint32_t hi = (uint16_t)(int16_t)profile_score(iq.qb, iq.lb, a.matrix,
+                                                                         a.alphabet, row0 + b, r);
+                    v[b] = lo | (hi << 16);
+                }
+                reinterpret_cast<uint4*>(prof)[idx] = make_uint4(v[0], v[1], v[2], v[3]);
+            }
+        }
+    };
+    template <int T, int R>
+    struct Cols {
+        uint4 w[R / 4];
+        __device__ __forceinline__ void load(const uint8_t* prof, uint32_t code, int t) {
+            load_chunks<T, R>(prof, code, t, w);
+        }
+        __device__ __forceinline__ uint32_t row(int l) const { return word_of(w[l / 4], l % 4); }
+    };
+};
+
+// One query, one database sequence per group, int32 lanes.
+struct ModeInt32 {
+    using Lane = LaneS32;
+    static constexpr bool kPairStream = false;
+    template <int T, int R>
+    struct Prof {
+        static constexpr int TR = T * R;
+        static constexpr size_t kBytes = (size_t)kProfileRows * TR * 4;
+        static __device__ __forceinline__ void stage(uint8_t* prof, const ItemQuery& iq,
+                                                     const WavefrontArgs& a, uint32_t p) {
+            for (uint32_t idx = threadIdx.x; idx < kProfileRows * (TR / 4); idx += kThreads) {
+                const uint32_t r = idx / (TR / 4), rem = idx % (TR / 4);
+                const uint32_t c = rem / T, t = rem % T;
+                const uint32_t row0 = p * TR + t * R + c * 4;
+                int v[4];
+#pragma unroll
+                for (int b = 0; b < 4; ++b)
+                    v[b] = profile_score(iq.qa, iq.la, a.matrix, a.alphabet, row0 + b, r);
+                reinterpret_cast<int4*>(prof)[idx] = make_int4(v[0], v[1], v[2], v[3]);
+            }
+        }
+    };
+    template <int T, int R>
+    struct Cols {
+        uint4 w[R / 4];
+        __device__ __forceinline__ void load(const uint8_t* prof, uint32_t code, int t) {
+            load_chunks<T, R>(prof, code, t, w);
+        }
+        __device__ __forceinline__ int32_t row(int l) const { return (int32_t)word_of(w[l / 4], l % 4); }
+    };
 };
 
 // Aligns every unit of one chunk (kWarps warps x 32/T groups) against the
-// whole query. All warps of the block process the same chunk, pass by pass.
+// item's query (pair). All warps of the block process the same chunk, pass by
+// pass.
 //
 // Boundary rows: entry T + j of a slot half holds (H, E) of column j (entries
 // below T take the fill steps' writes and are never read). Thread 0 reads them
 // in aligned 4-column blocks; blocks at or past the unit's length L (a
 // multiple of 4) read as zero, which is safe for the pad columns there: every
 // value they produce stays at or below the largest real H.
-template <int T, int R, bool PAIR>
+template <class Mode, int T, int R>
 __device__ __forceinline__ void process_chunk(const WavefrontArgs& a, const BinArgs& bin,
-                                              uint64_t base, uint64_t n_units, uint8_t* prof,
-                                              int32_t thr16) {
-    using Lane = typename std::conditional<PAIR, LaneS16x2, LaneS32>::type;
+                                              uint64_t base, uint64_t n_units,
+                                              const ItemQuery& iq, uint8_t* prof, int32_t thr16) {
+    using Lane = typename Mode::Lane;
     using V = typename Lane::V;
+    using Prof = typename Mode::template Prof<T, R>;
     constexpr int G = 32 / T;           // groups per warp
     constexpr int TR = T * R;           // query rows per pass
+    constexpr bool kPair = Mode::kPairStream;
     constexpr uint32_t kPadPair = kPadCode | (kPadCode << 8);
     constexpr uint32_t kPadWord = kPadPair | (kPadPair << 16);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = lane / T, t = lane % T;
-    const uint32_t P = (a.qlen + TR - 1) / TR;
+    const uint32_t qmax = iq.la > iq.lb ? iq.la : iq.lb;
+    const uint32_t P = (qmax + TR - 1) / TR;
     const uint64_t slot = ((uint64_t)blockIdx.x * kWarps + warp) * G + g;
     const uint64_t half = bin.bstride / 2;
     uint2* const bnd0 = bin.boundary + slot * bin.bstride;
@@ -195,13 +254,12 @@ __device__ __forceinline__ void process_chunk(const WavefrontArgs& a, const BinA
     // ---- locate this group's unit ----
     const uint64_t u = base + (uint64_t)warp * G + g;
     const bool have = u < n_units;
-    uint64_t sp = 0;  // sorted position (first sequence of the pair)
+    uint64_t sp = 0;  // sorted position (the first sequence of the pair for kPair)
     uint32_t L = 0;
     const uint8_t* stream = a.tile_data;
-    uint32_t half_sel = 0;  // int32 lanes: which sequence of the pair stream
+    uint32_t half_sel = 0;  // one-sequence modes: which sequence of the pair stream
     if (have) {
-        if (PAIR) sp = 2 * (bin.first_unit + u);
-        else sp = bin.unit_list ? (uint64_t)bin.unit_list[u] : bin.first_unit + u;
+        sp = kPair ? 2 * (bin.first_unit + u) : bin.first_unit + u;
         const uint64_t tile = sp / kTileSeqs;
         const uint32_t pslot = (uint32_t)((sp >> 1) & (kTilePairs - 1));
         L = a.tile_len[tile];
@@ -217,14 +275,14 @@ __device__ __forceinline__ void process_chunk(const WavefrontArgs& a, const BinA
     V best = vzero;
     for (uint32_t p = 0; p < P; ++p) {
         __syncthreads();  // every warp is done with the previous pass's profile
-        Profile<T, R, PAIR>::stage(prof, a, p);
+        Prof::stage(prof, iq, a, p);
         __syncthreads();
 
         V Hl[R], Fr[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) { Hl[r] = vzero; Fr[r] = vzero; }
         V hb_out = vzero, eb_out = vzero, hdiag0 = vzero;
-        uint32_t code_out = PAIR ? kPadPair : kPadCode;
+        uint32_t code_out = kPair ? kPadPair : kPadCode;
         const uint2* const bnd_in = bnd0 + (p & 1) * half + T;
         uint2* const bnd_out = bnd0 + ((p + 1) & 1) * half + T;
         const bool read_bnd = p > 0;
@@ -259,27 +317,28 @@ __device__ __forceinline__ void process_chunk(const WavefrontArgs& a, const BinA
                 uint32_t code = __shfl_up_sync(0xffffffffu, code_out, 1, T);
                 if (t == 0) {
                     const uint32_t w = (k < 2) ? wq.x : wq.y;
-                    code = PAIR ? ((w >> (16 * (k & 1))) & 0xffffu)
-                                : ((w >> (16 * (k & 1) + 8 * half_sel)) & 0xffu);
+                    code = kPair ? ((w >> (16 * (k & 1))) & 0xffffu)
+                                 : ((w >> (16 * (k & 1) + 8 * half_sel)) & 0xffu);
                     const uint4& bq = (k < 2) ? bq0 : bq1;
                     h_in = (V)((k & 1) ? bq.z : bq.x);
                     e_in = (V)((k & 1) ? bq.w : bq.y);
                 }
                 code_out = code;
-                ColumnScores<T, R, PAIR> cs;
-                cs.load(prof, PAIR ? (code & 0xffu) : code, code >> 8, t);
+                typename Mode::template Cols<T, R> cs;
+                cs.load(prof, code, t);
                 V diag = hdiag0;
                 V E = e_in;
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
-                    const V sc = cs.row(r);
-                    const V H = Lane::max3_relu(Lane::vadd(diag, sc), E, Fr[r]);  // H[i][j]
+                    const V sc = (V)cs.row(r);
+                    const V x = Lane::vadd(diag, sc);              // H[i-1][j-1] + fsbt
+                    const V H = Lane::max3_relu(x, E, Fr[r]);      // H[i][j]
                     diag = Hl[r];                                  // H[i][j-1]: diagonal of row i+1
                     Hl[r] = H;
                     const V hb = Lane::vadd(H, vbeta);             // H[i][j] - beta
                     E = Lane::addmax(E, valpha, hb);               // E[i+1][j]
                     Fr[r] = Lane::addmax(Fr[r], valpha, hb);       // F[i][j+1]
-                    best = Lane::vmax(best, H);
+                    best = Lane::vmax(best, x);                    // max H = max(0, max x)
                 }
                 hb_out = Hl[R - 1];
                 eb_out = E;
@@ -297,36 +356,58 @@ __device__ __forceinline__ void process_chunk(const WavefrontArgs& a, const BinA
 #pragma unroll
     for (int o = T / 2; o > 0; o >>= 1)
         best = Lane::vmax(best, (V)__shfl_xor_sync(0xffffffffu, (uint32_t)best, o, T));
-    if (have && t == 0) {
-        if (PAIR) {
+    if (!have || t != 0) return;
+    if constexpr (std::is_same<Lane, LaneS32>::value) {
+        const uint32_t id = a.sorted_ids[sp];
+        if (id != 0xffffffffu) a.scores[(uint64_t)iq.ia * a.score_stride + id] = (int32_t)best;
+    } else {
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int32_t v = (int16_t)(h ? ((uint32_t)best >> 16) : ((uint32_t)best & 0xffffu));
-                const uint32_t id = a.sorted_ids[sp + h];
-                if (id == 0xffffffffu) continue;
-                if (v >= thr16) {
-                    const uint32_t k = atomicAdd(a.flag_count, 1u);
-                    a.flag_list[k] = (uint32_t)(sp + h);
-                } else {
-                    a.scores[id] = v;
-                }
-            }
+    for (int h = 0; h < 2; ++h) {
+        const int32_t v = (int16_t)(h ? ((uint32_t)best >> 16) : ((uint32_t)best & 0xffffu));
+        const uint64_t seq = kPair ? sp + h : sp;
+        const uint32_t qi = kPair ? iq.ia : (h ? iq.ib : iq.ia);
+        const uint32_t id = a.sorted_ids[seq];
+        if (id == 0xffffffffu || qi == 0xffffffffu) continue;
+        if (v >= thr16) {  // rescored in int32; -1 marks it until then
+            const uint32_t k = atomicAdd(a.flag_count, 1u);
+            if (k < a.flag_cap) a.flag_list[k] = make_uint2(qi, (uint32_t)seq);
+            a.scores[(uint64_t)qi * a.score_stride + id] = -1;
         } else {
-            const uint32_t id = a.sorted_ids[sp];
-            if (id != 0xffffffffu) a.scores[id] = (int32_t)best;
+            a.scores[(uint64_t)qi * a.score_stride + id] = v;
         }
+    }
     }
 }
 
-// Persistent search kernel over the two bins of a database. Chunks of bin 0
-// (the long sequences, a warp per pair: TL lanes x RL rows) are handed out
-// first, then chunks of bin 1 (TS lanes per pair x RS rows), so the longest
-// work starts first. Bin 0 may instead be an explicit list of sorted
-// positions (int32 rescoring).
-template <int TS, int RS, int TL, int RL, bool PAIR>
+__device__ __forceinline__ ItemQuery item_query(const WavefrontArgs& a, uint32_t k) {
+    ItemQuery iq;
+    if (a.pairs) {
+        const QueryPair qp = a.pairs[k];
+        iq.qa = a.query + qp.off_a;
+        iq.qb = a.query + qp.off_b;
+        iq.la = qp.len_a;
+        iq.lb = qp.len_b;
+        iq.ia = qp.q_a;
+        iq.ib = qp.q_b;
+    } else {
+        iq.qa = iq.qb = a.query;
+        iq.la = a.qlen;
+        iq.lb = 0;
+        iq.ia = 0;
+        iq.ib = 0xffffffffu;
+    }
+    return iq;
+}
+
+// Persistent search kernel. Work items are (chunk, query item) pairs, chunk
+// major: chunks of bin 0 (the long sequences, a warp per unit: TL lanes x RL
+// rows) first, then chunks of bin 1 (TS lanes per unit x RS rows), so the
+// longest work starts first and one database chunk is reused across the
+// query items from L2.
+template <class Mode, int TS, int RS, int TL, int RL>
 __global__ void __launch_bounds__(kThreads) search_kernel(const WavefrontArgs a) {
     extern __shared__ __align__(16) uint8_t prof[];
-    __shared__ uint32_t s_chunk, s_units;
+    __shared__ uint32_t s_item;
     constexpr uint32_t UNITS_L = kWarps * (32 / TL);
     constexpr uint32_t UNITS_S = kWarps * (32 / TS);
 
@@ -334,58 +415,68 @@ __global__ void __launch_bounds__(kThreads) search_kernel(const WavefrontArgs a)
     __shared__ int s_smax;
     if (threadIdx.x == 0) s_smax = 0;
     __syncthreads();
-    if (PAIR) {
-        int mx = 0;
-        for (uint32_t i = threadIdx.x; i < a.alphabet * a.alphabet; i += kThreads)
-            mx = max(mx, (int)a.matrix[i]);
-        atomicMax(&s_smax, mx);
-        __syncthreads();
-    }
+    int mx = 0;
+    for (uint32_t i = threadIdx.x; i < a.alphabet * a.alphabet; i += kThreads)
+        mx = max(mx, (int)a.matrix[i]);
+    atomicMax(&s_smax, mx);
+    __syncthreads();
     const int32_t thr16 = 32767 - s_smax;
 
+    const uint32_t n_items_q = a.pairs ? a.n_pairs : 1u;
+    const uint64_t chunks_long = (a.bin[0].n_units + UNITS_L - 1) / UNITS_L;
+    const uint64_t chunks_short = (a.bin[1].n_units + UNITS_S - 1) / UNITS_S;
+    const uint64_t items_long = chunks_long * n_items_q;
+    const uint64_t items = items_long + chunks_short * n_items_q;
     for (;;) {
-        if (threadIdx.x == 0) {
-            s_chunk = atomicAdd(a.work_counter, 1u);
-            s_units = a.bin[0].unit_list ? *a.bin[0].unit_count : 0u;
-        }
+        if (threadIdx.x == 0) s_item = atomicAdd(a.work_counter, 1u);
         __syncthreads();
-        const uint64_t n_long = a.bin[0].unit_list ? (uint64_t)s_units : a.bin[0].n_units;
-        const uint64_t chunks_long = (n_long + UNITS_L - 1) / UNITS_L;
-        const uint64_t c = s_chunk;
-        if (c < chunks_long) {
-            process_chunk<TL, RL, PAIR>(a, a.bin[0], c * UNITS_L, n_long, prof, thr16);
+        const uint64_t it = s_item;
+        if (it >= items) break;
+        if (it < items_long) {
+            const ItemQuery iq = item_query(a, (uint32_t)(it % n_items_q));
+            process_chunk<Mode, TL, RL>(a, a.bin[0], (it / n_items_q) * UNITS_L, a.bin[0].n_units,
+                                        iq, prof, thr16);
         } else {
-            const uint64_t base = (c - chunks_long) * UNITS_S;
-            if (base >= a.bin[1].n_units) break;
-            process_chunk<TS, RS, PAIR>(a, a.bin[1], base, a.bin[1].n_units, prof, thr16);
+            const uint64_t is = it - items_long;
+            const ItemQuery iq = item_query(a, (uint32_t)(is % n_items_q));
+            process_chunk<Mode, TS, RS>(a, a.bin[1], (is / n_items_q) * UNITS_S, a.bin[1].n_units,
+                                        iq, prof, thr16);
         }
-        __syncthreads();  // s_chunk is rewritten by the next iteration
+        __syncthreads();  // s_item is rewritten by the next iteration
     }
 }
 
 using KernelFn = void (*)(WavefrontArgs);
 
 struct Entry {
+    int mode;  // KernelChoice::Mode
     int R;
-    bool pair;
     KernelFn fn;
     size_t smem;
 };
 
-#define SWGB_ENTRY(R, P)                                                           \
-    {R, P, search_kernel<kShortT, R, kLongT, kLongR, P>,                           \
-     (Profile<kShortT, R, P>::kBytes > Profile<kLongT, kLongR, P>::kBytes         \
-          ? Profile<kShortT, R, P>::kBytes                                         \
-          : Profile<kLongT, kLongR, P>::kBytes)}
+template <class Mode, int R>
+constexpr size_t smem_of() {
+    return Mode::template Prof<kShortT, R>::kBytes > Mode::template Prof<kLongT, kLongR>::kBytes
+               ? Mode::template Prof<kShortT, R>::kBytes
+               : Mode::template Prof<kLongT, kLongR>::kBytes;
+}
+
+#define SWGB_ENTRY(M, MODE, R) \
+    {M, R, search_kernel<MODE, kShortT, R, kLongT, kLongR>, smem_of<MODE, R>()}
 const Entry kEntries[] = {
-    SWGB_ENTRY(8, true),  SWGB_ENTRY(12, true), SWGB_ENTRY(16, true),
-    SWGB_ENTRY(20, true), SWGB_ENTRY(24, true), SWGB_ENTRY(16, false),
+    SWGB_ENTRY(0, ModePairDb, 8),     SWGB_ENTRY(0, ModePairDb, 12),
+    SWGB_ENTRY(0, ModePairDb, 16),    SWGB_ENTRY(0, ModePairDb, 20),
+    SWGB_ENTRY(0, ModePairDb, 24),    SWGB_ENTRY(1, ModeQueryPair, 8),
+    SWGB_ENTRY(1, ModeQueryPair, 12), SWGB_ENTRY(1, ModeQueryPair, 16),
+    SWGB_ENTRY(1, ModeQueryPair, 20), SWGB_ENTRY(1, ModeQueryPair, 24),
+    SWGB_ENTRY(2, ModeInt32, 16),
 };
 #undef SWGB_ENTRY
 
 const Entry* find_entry(const KernelChoice& kc) {
     for (const Entry& e : kEntries)
-        if (e.R == kc.R && e.pair == kc.pair) return &e;
+        if (e.R == kc.R && e.mode == (int)kc.mode) return &e;
     return nullptr;
 }
 
@@ -423,9 +514,8 @@ cudaError_t launch_wavefront(const KernelChoice& kc, const WavefrontArgs& a, int
     return cudaGetLastError();
 }
 
-// Longest pad needed past a unit's last column by the boundary rows.
+// Entries past a unit's length that a boundary row half must hold.
 uint32_t boundary_slack() { return 2 * kLongT + 8; }
-
 
 // ---------------------------------------------------------------------------
 // Database layout kernels
