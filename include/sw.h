@@ -211,6 +211,64 @@ sw_status sw_search_batch_device(sw_db* db, uint32_t nq, const uint8_t* d_querie
                                  int32_t* d_top_scores, uint64_t* d_top_index, void* stream);
 
 /*
+ * Serving: a continuous-batching server over a loaded database (the paper
+ * searches one query at a time; this keeps the database resident and takes
+ * queries as they arrive).
+ *
+ * The database is cut into `slices` parts of about equal work. A scheduler
+ * thread runs waves; one wave advances every admitted query by one slice in a
+ * single persistent launch (two queries at the same slice share the 16-bit
+ * lane halves). A query is admitted at a wave boundary when a slot is free: a
+ * slot reserves the device memory one query needs (a score row of n_seqs
+ * int32 and max_qlen code bytes), and the number of slots is bounded by
+ * max_active and by device_budget, so admission is by device memory. Queries
+ * that arrive while others are on the GPU join the next wave; a query leaves
+ * after its last slice with its exact top-k list. Requests whose scoring
+ * scheme (matrix, alpha, beta) differs from the running ones wait until those
+ * drain. While a server exists, use the database only through it.
+ */
+typedef struct sw_server sw_server;
+
+typedef struct {
+    uint32_t max_queue;        /* waiting requests beyond which submit fails SW_ERR_BUSY (4096) */
+    uint32_t max_active;       /* query slots (64) */
+    uint32_t max_qlen;         /* longest accepted query (8192) */
+    uint32_t slices;           /* database slices per query (8) */
+    uint64_t device_budget;    /* bytes for the slots (0 = max_active slots) */
+} sw_server_opts;
+
+typedef struct {
+    double submit_ms;          /* times in ms since the server was created */
+    double admit_ms;
+    double done_ms;
+} sw_latency;
+
+typedef struct {
+    uint64_t waves, completed, rejected;
+    uint64_t cells;            /* DP cells of the completed queries */
+    double busy_ms;            /* wall time spent in waves */
+    uint32_t pending, active, max_active, slices;
+} sw_server_stats;
+
+/* Create a server (starts its scheduler thread). opts may be NULL. */
+sw_status sw_server_create(sw_db* db, const sw_server_opts* opts, sw_server** out);
+/* Queue one query (HOST buffers, copied before returning); receives a ticket. */
+sw_status sw_server_submit(sw_server* srv, const uint8_t* query, uint32_t qlen,
+                           const int8_t* matrix, int32_t alpha, int32_t beta, uint32_t top_k,
+                           uint64_t* ticket);
+/* Wait up to timeout_ms for a ticket: top_k results (HOST) and its timestamps.
+ * SW_ERR_TIMEOUT if not done in time (the ticket stays valid); a finished
+ * ticket is consumed. */
+sw_status sw_server_wait(sw_server* srv, uint64_t ticket, uint32_t timeout_ms,
+                         int32_t* top_scores, uint64_t* top_index, uint32_t* n_top,
+                         sw_latency* lat);
+/* Drop a ticket: a waiting request never runs, a running one leaves at the next wave. */
+sw_status sw_server_cancel(sw_server* srv, uint64_t ticket);
+sw_status sw_server_get_stats(sw_server* srv, sw_server_stats* out);
+/* Stop the scheduler (outstanding requests are cancelled) and free the server. */
+void sw_server_destroy(sw_server* srv);
+
+/*
  * Score one query against caller-owned device sequences WITHOUT allocating
  * any device memory. The paper has no counterpart to this call; it exists for
  * callers that may not call cudaMalloc, for example a host application that

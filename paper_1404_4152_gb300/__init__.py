@@ -66,6 +66,25 @@ class sw_profile(ctypes.Structure):
                 ("cells", ctypes.c_uint64 * 4), ("ms", ctypes.c_double * 4)]
 
 
+class sw_server_opts(ctypes.Structure):
+    _fields_ = [("max_queue", ctypes.c_uint32), ("max_active", ctypes.c_uint32),
+                ("max_qlen", ctypes.c_uint32), ("slices", ctypes.c_uint32),
+                ("device_budget", ctypes.c_uint64)]
+
+
+class sw_latency(ctypes.Structure):
+    _fields_ = [("submit_ms", ctypes.c_double), ("admit_ms", ctypes.c_double),
+                ("done_ms", ctypes.c_double)]
+
+
+class sw_server_stats(ctypes.Structure):
+    _fields_ = [("waves", ctypes.c_uint64), ("completed", ctypes.c_uint64),
+                ("rejected", ctypes.c_uint64), ("cells", ctypes.c_uint64),
+                ("busy_ms", ctypes.c_double), ("pending", ctypes.c_uint32),
+                ("active", ctypes.c_uint32), ("max_active", ctypes.c_uint32),
+                ("slices", ctypes.c_uint32)]
+
+
 # Every entry point the header declares: (name, restype, argtypes).
 _P, _U8, _U32, _U64, _I32 = (ctypes.c_void_p, ctypes.c_uint8, ctypes.c_uint32, ctypes.c_uint64,
                              ctypes.c_int32)
@@ -81,6 +100,12 @@ SIGNATURES = {
                                               _P]),
     "sw_search_noalloc": (ctypes.c_int, [_P, _U32, _P, _U32, _I32, _I32, _P, _P, _U32, _U32, _P,
                                          _P]),
+    "sw_server_create": (ctypes.c_int, [_P, _P, ctypes.POINTER(_P)]),
+    "sw_server_submit": (ctypes.c_int, [_P, _P, _U32, _P, _I32, _I32, _U32, _P]),
+    "sw_server_wait": (ctypes.c_int, [_P, _U64, _U32, _P, _P, _P, _P]),
+    "sw_server_cancel": (ctypes.c_int, [_P, _U64]),
+    "sw_server_get_stats": (ctypes.c_int, [_P, _P]),
+    "sw_server_destroy": (None, [_P]),
     "sw_db_get_profile": (ctypes.c_int, [_P, _P]),
     "sw_db_reset_profile": (ctypes.c_int, [_P]),
     "sw_last_error": (ctypes.c_char_p, []),
@@ -282,6 +307,87 @@ def sw_db_get_profile(db: Database) -> dict:
 
 def sw_db_reset_profile(db: Database):
     _check(load_library().sw_db_reset_profile(db.handle))
+
+
+class Server:
+    """A continuous-batching search server (an ``sw_server*``) over a loaded database."""
+
+    def __init__(self, handle, db: Database):
+        self.handle = handle
+        self.db = db
+
+    def submit(self, query, matrix, alpha: int, beta: int, top_k: int = 10) -> int:
+        return sw_server_submit(self, query, matrix, alpha, beta, top_k)
+
+    def wait(self, ticket: int, timeout_ms: int = 600_000, top_k: int = SW_MAX_TOP_K):
+        return sw_server_wait(self, ticket, timeout_ms, top_k)
+
+    def cancel(self, ticket: int):
+        sw_server_cancel(self, ticket)
+
+    def stats(self) -> dict:
+        return sw_server_get_stats(self)
+
+    def destroy(self):
+        if self.handle:
+            load_library().sw_server_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.destroy()
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def sw_server_create(db: Database, max_queue: int = 0, max_active: int = 0, max_qlen: int = 0,
+                     slices: int = 0, device_budget: int = 0) -> Server:
+    opts = sw_server_opts(max_queue, max_active, max_qlen, slices, device_budget)
+    h = ctypes.c_void_p()
+    _check(load_library().sw_server_create(db.handle, ctypes.byref(opts), ctypes.byref(h)))
+    return Server(h, db)
+
+
+def sw_server_submit(srv: Server, query, matrix, alpha: int, beta: int, top_k: int = 10) -> int:
+    q = np.ascontiguousarray(query, dtype=np.uint8)
+    m = np.ascontiguousarray(matrix, dtype=np.int8)
+    t = ctypes.c_uint64()
+    _check(load_library().sw_server_submit(srv.handle, _ptr(q), q.size, _ptr(m), int(alpha),
+                                           int(beta), int(top_k), ctypes.byref(t)))
+    return t.value
+
+
+def sw_server_wait(srv: Server, ticket: int, timeout_ms: int = 600_000,
+                   top_k: int = SW_MAX_TOP_K):
+    """-> (top_scores, top_index, latency dict); raises SwError (SW_ERR_TIMEOUT, ...)."""
+    ts = np.zeros(max(top_k, 1), np.int32)
+    ti = np.zeros(max(top_k, 1), np.uint64)
+    n = ctypes.c_uint32()
+    lat = sw_latency()
+    _check(load_library().sw_server_wait(srv.handle, int(ticket), int(timeout_ms), _ptr(ts),
+                                         _ptr(ti), ctypes.byref(n), ctypes.byref(lat)))
+    k = n.value
+    return ts[:k].copy(), ti[:k].copy(), {f: getattr(lat, f) for f, _ in sw_latency._fields_}
+
+
+def sw_server_cancel(srv: Server, ticket: int):
+    _check(load_library().sw_server_cancel(srv.handle, int(ticket)))
+
+
+def sw_server_get_stats(srv: Server) -> dict:
+    st = sw_server_stats()
+    _check(load_library().sw_server_get_stats(srv.handle, ctypes.byref(st)))
+    return {f: getattr(st, f) for f, _ in sw_server_stats._fields_}
+
+
+def sw_server_destroy(srv: Server):
+    srv.destroy()
 
 
 def sw_last_error() -> str:

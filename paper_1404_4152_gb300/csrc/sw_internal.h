@@ -58,6 +58,10 @@ struct WavefrontArgs {
     uint32_t qlen;                  // single query length
     const QueryPair* pairs;         // batch: query pairs (NULL for a single query)
     uint32_t n_pairs;
+    // serving waves: pair k covers bin-1 chunks pair_chunk0[k] .. + (item_prefix[k+1] -
+    // item_prefix[k]); NULL = every pair covers both whole bins
+    const uint32_t* item_prefix;    // n_pairs + 1
+    const uint32_t* pair_chunk0;    // n_pairs
     const int8_t* matrix;
     uint32_t alphabet;
     int32_t alpha, beta;
@@ -113,6 +117,7 @@ cudaError_t launch_wavefront(const KernelChoice& kc, const WavefrontArgs& a, int
 int wavefront_occupancy(const KernelChoice& kc, int* threads_per_block);
 bool wavefront_supported(const KernelChoice& kc);
 int wavefront_block_threads();
+int wavefront_short_units_per_chunk();  // sequences per short-bin chunk (one-sequence modes)
 
 // Tile layout: gather database residues into tiles (device side).
 cudaError_t launch_build_tiles(const uint8_t* residues, const uint64_t* offsets,

@@ -422,6 +422,26 @@ __global__ void __launch_bounds__(kThreads) search_kernel(const WavefrontArgs a)
     __syncthreads();
     const int32_t thr16 = 32767 - s_smax;
 
+    if (a.item_prefix) {
+        // serving wave: each pair scans its own range of bin-1 chunks
+        const uint32_t items = a.item_prefix[a.n_pairs];
+        for (;;) {
+            if (threadIdx.x == 0) s_item = atomicAdd(a.work_counter, 1u);
+            __syncthreads();
+            const uint32_t it = s_item;
+            if (it >= items) break;
+            uint32_t lo = 0, hi = a.n_pairs;
+            while (hi - lo > 1) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (a.item_prefix[mid] <= it) lo = mid; else hi = mid;
+            }
+            const uint64_t chunk = (uint64_t)a.pair_chunk0[lo] + (it - a.item_prefix[lo]);
+            process_chunk<Mode, TS, RS>(a, a.bin[1], chunk * UNITS_S, a.bin[1].n_units,
+                                        item_query(a, lo), prof, thr16);
+            __syncthreads();
+        }
+        return;
+    }
     const uint32_t n_items_q = a.pairs ? a.n_pairs : 1u;
     const uint64_t chunks_long = (a.bin[0].n_units + UNITS_L - 1) / UNITS_L;
     const uint64_t chunks_short = (a.bin[1].n_units + UNITS_S - 1) / UNITS_S;
@@ -484,6 +504,7 @@ const Entry* find_entry(const KernelChoice& kc) {
 
 bool wavefront_supported(const KernelChoice& kc) { return find_entry(kc) != nullptr; }
 int wavefront_block_threads() { return kThreads; }
+int wavefront_short_units_per_chunk() { return kWarps * (32 / kShortT); }
 
 int wavefront_occupancy(const KernelChoice& kc, int* threads_per_block) {
     const Entry* e = find_entry(kc);
