@@ -64,6 +64,11 @@ def parse_args():
                    help="timed steps of the batched workload (0 skips it)")
     p.add_argument("--batch-seqs", type=int, default=1_000_000)
     p.add_argument("--batch-queries", type=int, default=256)
+    p.add_argument("--serve-seqs", type=int, default=20_000_000)
+    p.add_argument("--serve-rates", default="1.0",
+                   help="comma-separated Poisson arrival rates (queries/s); empty skips serving")
+    p.add_argument("--serve-arrivals", type=int, default=16)
+    p.add_argument("--no-tune", action="store_true")
     return p.parse_args()
 
 
@@ -175,6 +180,8 @@ def run_batched(args, sw, torch, dev, rank):
     graph-captured persistent launch per step; GCUPS and the kernel-phase time."""
     w = synth.config2(seed=1406 + 1000 * rank, n_seqs=args.batch_seqs, n_queries=args.batch_queries)
     db = sw.sw_db_load(w.residues, w.offsets, alphabet=20, flags=sw.SW_DB_FLAG_PROFILE)
+    if not args.no_tune:
+        sw.sw_db_autotune(db, w.matrix, w.alpha, w.beta)
     qlens = [int(q.size) for q in w.queries]
     qoff = np.concatenate([[0], np.cumsum(qlens)]).astype(np.uint64)
     nq, n, k = len(qlens), w.n_seqs, w.top_k
@@ -207,6 +214,68 @@ def run_batched(args, sw, torch, dev, rank):
                         f"persistent launch per step",
             "value": cells / (ms / 1e3) / 1e9, "unit": "GCUPS", "steps": args.batch_steps,
             "ms_per_step": ms / args.batch_steps, "gpu_launches": int(prof["launches"])}
+
+
+def run_served(args, sw, rank):
+    """Serving: a resident database of 20,000,000 sequences; Poisson arrivals of queries
+    (log-normal lengths, median 300); p50/p99 latency and sustained GCUPS per rate."""
+    import threading
+
+    rates = [float(r) for r in args.serve_rates.split(",") if r.strip()]
+    if not rates:
+        return None
+    res, off = synth.make_db(args.serve_seqs, 1407 + 1000 * rank)
+    db = sw.sw_db_load(res, off, alphabet=20)
+    if not args.no_tune:
+        sw.sw_db_autotune(db, synth.BLOSUM62, 1, 11)
+    n_res = int(off[-1])
+    del res
+    out = []
+    for ri, rate in enumerate(rates):
+        lens = synth.config3_query_lengths(args.serve_arrivals, 1407 + ri)
+        qs = synth.make_queries(lens, 1407 + ri)
+        arrive = synth.arrival_times(len(qs), rate, 1407 + ri)
+        srv = sw.sw_server_create(db, max_active=32, slices=8)
+        tickets = [None] * len(qs)
+        rejected = [0]
+        t0 = time.perf_counter()
+
+        def submitter():
+            for i, q in enumerate(qs):
+                d = arrive[i] - (time.perf_counter() - t0)
+                if d > 0:
+                    time.sleep(d)
+                try:
+                    tickets[i] = srv.submit(q, synth.BLOSUM62, 1, 11, 10)
+                except sw.SwError:
+                    rejected[0] += 1
+
+        th = threading.Thread(target=submitter)
+        th.start()
+        th.join()
+        lat = []
+        cells = 0
+        for i, tk in enumerate(tickets):
+            if tk is None:
+                continue
+            _, _, l = srv.wait(tk)
+            lat.append(l["done_ms"] - l["submit_ms"])
+            cells += int(qs[i].size) * n_res
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+        srv.destroy()
+        lat = np.array(lat)
+        out.append({"rate_qps": rate, "arrivals": len(qs), "completed": int(lat.size),
+                    "rejected": rejected[0], "p50_ms": float(np.percentile(lat, 50)),
+                    "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
+                    "sustained_gcups": cells / wall / 1e9,
+                    "busy_gcups": cells / (st["busy_ms"] / 1e3) / 1e9 if st["busy_ms"] else None,
+                    "waves": st["waves"]})
+    db.free()
+    return {"workload": f"config3: {args.serve_seqs:,} resident sequences ({n_res / 1e9:.2f} G aa); "
+                        f"Poisson arrivals, query lengths log-normal median 300 [20, 5000]; "
+                        f"32 query slots, 8 slices",
+            "rates": out}
 
 
 def run_reference(args):
@@ -256,6 +325,7 @@ def run_ours(args):
 
     w = build_workload(args, rank)
     db = sw.sw_db_load(w.residues, w.offsets, alphabet=20, device=local, flags=sw.SW_DB_FLAG_PROFILE)
+    tuning = None if args.no_tune else sw.sw_db_autotune(db, w.matrix, w.alpha, w.beta)
     n = w.n_seqs
     qlens = [int(q.size) for q in w.queries]
     qoff = np.concatenate([[0], np.cumsum(qlens)]).astype(np.int64)
@@ -387,6 +457,8 @@ def run_ours(args):
                "h2d_bytes_per_step": int(sum(qlens) + len(qlens) * w.matrix.size),
                "d2h_bytes_per_step": int(len(qlens) * (4 * n + 12 * k + 4))}
 
+    served = run_served(args, sw, rank) if args.serve_rates.strip() else None
+
     batched = None
     if args.batch_steps > 0:
         batched = run_batched(args, sw, torch, dev, rank)
@@ -409,6 +481,8 @@ def run_ours(args):
         "gpu_launches": int(prof["launches"]),
         "phases_ms": {p: ph[p]["ms"] for p in ph},
         "batched": batched,
+        "served": served,
+        "tuning": tuning,
         "per_query": per_query,
         "context": {"paper_xeon_phi_gcups_max": PAPER_PHI_GCUPS_MAX},
     }

@@ -211,6 +211,30 @@ sw_status sw_search_batch_device(sw_db* db, uint32_t nq, const uint8_t* d_querie
                                  int32_t* d_top_scores, uint64_t* d_top_index, void* stream);
 
 /*
+ * Autotuning (no counterpart in the paper, which fixes its kernel shapes; the
+ * score-profile width N = 8 of Section III.B.3 is the nearest analogue).
+ * Times the search kernel on a sample of this database for every kernel mode
+ * (index 0: one query against pairs of database sequences; 1: two queries per
+ * lane pair, used by batches and the server; 2: int32) and every rows-per-lane
+ * choice R in {8, 12, 16, 20, 24}, and stores the device time per query row
+ * and database residue. Later searches on the handle pick R by minimising
+ * padded rows x measured cost. int32_over_int16 is the measured speed ratio;
+ * cutover_fraction the share of saturating pairs above which a search would be
+ * cheaper in int32 (the 16/32-bit cutover). cache_path (may be NULL) names a
+ * JSON file reused when its GPU name and SM count match.
+ */
+typedef struct {
+    double ns_per_row_residue[3][5];
+    uint32_t fastest_R[3];
+    double int32_over_int16;
+    double cutover_fraction;
+    int from_cache;
+} sw_tuning;
+
+sw_status sw_db_autotune(sw_db* db, const int8_t* matrix, int32_t alpha, int32_t beta,
+                         const char* cache_path, sw_tuning* out);
+
+/*
  * Serving: a continuous-batching server over a loaded database (the paper
  * searches one query at a time; this keeps the database resident and takes
  * queries as they arrive).

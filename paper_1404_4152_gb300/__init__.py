@@ -85,6 +85,12 @@ class sw_server_stats(ctypes.Structure):
                 ("slices", ctypes.c_uint32)]
 
 
+class sw_tuning(ctypes.Structure):
+    _fields_ = [("ns_per_row_residue", (ctypes.c_double * 5) * 3),
+                ("fastest_R", ctypes.c_uint32 * 3), ("int32_over_int16", ctypes.c_double),
+                ("cutover_fraction", ctypes.c_double), ("from_cache", ctypes.c_int)]
+
+
 # Every entry point the header declares: (name, restype, argtypes).
 _P, _U8, _U32, _U64, _I32 = (ctypes.c_void_p, ctypes.c_uint8, ctypes.c_uint32, ctypes.c_uint64,
                              ctypes.c_int32)
@@ -106,6 +112,7 @@ SIGNATURES = {
     "sw_server_cancel": (ctypes.c_int, [_P, _U64]),
     "sw_server_get_stats": (ctypes.c_int, [_P, _P]),
     "sw_server_destroy": (None, [_P]),
+    "sw_db_autotune": (ctypes.c_int, [_P, _P, _I32, _I32, ctypes.c_char_p, _P]),
     "sw_db_get_profile": (ctypes.c_int, [_P, _P]),
     "sw_db_reset_profile": (ctypes.c_int, [_P]),
     "sw_last_error": (ctypes.c_char_p, []),
@@ -388,6 +395,21 @@ def sw_server_get_stats(srv: Server) -> dict:
 
 def sw_server_destroy(srv: Server):
     srv.destroy()
+
+
+def sw_db_autotune(db: Database, matrix, alpha: int, beta: int, cache_path: str | None = None):
+    """Measure every kernel shape on a sample of the database; later searches use the best."""
+    m = np.ascontiguousarray(matrix, dtype=np.int8)
+    t = sw_tuning()
+    _check(load_library().sw_db_autotune(db.handle, _ptr(m), int(alpha), int(beta),
+                                         cache_path.encode() if cache_path else None,
+                                         ctypes.byref(t)))
+    modes = ("pair_db", "query_pair", "int32")
+    return {"ns_per_row_residue": {modes[i]: list(t.ns_per_row_residue[i]) for i in range(3)},
+            "rows_per_lane": [8, 12, 16, 20, 24],
+            "fastest_R": {modes[i]: t.fastest_R[i] for i in range(3)},
+            "int32_over_int16": t.int32_over_int16, "cutover_fraction": t.cutover_fraction,
+            "from_cache": bool(t.from_cache)}
 
 
 def sw_last_error() -> str:

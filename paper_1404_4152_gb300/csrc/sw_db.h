@@ -96,6 +96,10 @@ struct sw_db {
     DevBuf b_pairs, b_qoff, b_qlen, b_flags, b_topk, b_queries, b_scores, b_top;
     BatchGraph graph;
 
+    // autotuning (sw_db_autotune)
+    sw_tuning tuning{};
+    bool tuned = false;
+
     // residues of the sequences in each bin (for cell counts)
     uint64_t residues_short = 0, residues_long = 0;
 

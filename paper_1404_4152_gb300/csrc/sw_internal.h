@@ -26,6 +26,7 @@ constexpr uint32_t kTilePairs = 4;
 constexpr int kShortT = 8;
 constexpr int kLongT = 32;
 constexpr int kLongR = 16;
+constexpr int kTuneR = 5;  // rows-per-lane choices: 8, 12, 16, 20, 24
 
 // One bin of units: pairs of sequences (single-query packed kernels) or
 // single sequences (batched and int32 kernels) at sorted positions

@@ -33,16 +33,20 @@ constexpr int kRescoreGrid = 64;
 
 const int kShortR[] = {8, 12, 16, 20, 24};
 
-// Rows padded to whole passes times the per-step work (alu_per_row ALU
-// instructions per query row plus about 8 per step), summed over the items.
-int choose_R(const std::vector<uint32_t>& lengths, double alu_per_row) {
+// Rows padded to whole passes times the cost of a row: measured by the
+// autotuner when the handle has been tuned, else estimated as alu_per_row ALU
+// instructions per query row plus about 8 per step; summed over the items.
+int choose_R(const sw_db* db, int mode, const std::vector<uint32_t>& lengths, double alu_per_row) {
     int bestR = 16;
     double best = 1e300;
-    for (int R : kShortR) {
+    for (int i = 0; i < (int)(sizeof kShortR / sizeof kShortR[0]); ++i) {
+        const int R = kShortR[i];
         const uint32_t TR = (uint32_t)kShortT * R;
+        const double measured = db->tuned ? db->tuning.ns_per_row_residue[mode][i] : 0.0;
+        const double per_pass = measured > 0 ? measured * TR : (alu_per_row * R + 8.0);
         double cost = 0;
-        for (uint32_t m : lengths) cost += (double)((m + TR - 1) / TR) * (alu_per_row * R + 8.0);
-        if (R == 16) cost *= 0.97;
+        for (uint32_t m : lengths) cost += (double)((m + TR - 1) / TR) * per_pass;
+        if (measured <= 0 && R == 16) cost *= 0.97;
         if (cost < best) { best = cost; bestR = R; }
     }
     return bestR;
@@ -52,9 +56,9 @@ bool use_int32(const sw_db* db, int32_t alpha, int32_t beta) {
     return (db->flags & SW_DB_FLAG_FORCE_INT32) || (int64_t)alpha + beta > 32768;
 }
 
-KernelChoice single_choice(uint32_t qlen, bool i32) {
+KernelChoice single_choice(const sw_db* db, uint32_t qlen, bool i32) {
     if (i32) return KernelChoice{KernelChoice::kInt32, 16};
-    return KernelChoice{KernelChoice::kPairDb, choose_R({qlen}, 5.5)};
+    return KernelChoice{KernelChoice::kPairDb, choose_R(db, 0, {qlen}, 4.5)};
 }
 
 // Two halves per slot, each the longest unit plus the wavefront's slack.
@@ -272,7 +276,7 @@ sw_status enqueue_search(sw_db* db, const uint8_t* d_query, uint32_t qlen, const
     const bool i32 = use_int32(db, alpha, beta);
     if ((e = cudaMemsetAsync(db->d_counters, 0, 64, stream)) != cudaSuccess)
         return cuda_fail(e, "search: counter reset");
-    const KernelChoice kc = single_choice(qlen, i32);
+    const KernelChoice kc = single_choice(db, qlen, i32);
     {
         WavefrontArgs a = base_args(db, d_matrix, alpha, beta, d_scores, db->n_seqs,
                                     kc.mode == KernelChoice::kPairDb ? kTilePairs : kTileSeqs);
@@ -354,7 +358,7 @@ BatchPlan plan_batch(const sw_db* db, uint32_t nq, const uint64_t* qoffsets) {
         pl.pairs.push_back(p);
         item_len.push_back(std::max(p.len_a, p.len_b));
     }
-    pl.kc = KernelChoice{KernelChoice::kQueryPair, choose_R(item_len, 4.5)};
+    pl.kc = KernelChoice{KernelChoice::kQueryPair, choose_R(db, 1, item_len, 3.5)};
     for (uint32_t q = 0; q < nq; ++q) pl.cells += (uint64_t)pl.qlen[q] * db->total_residues;
     pl.flag_cap = (uint32_t)std::min<uint64_t>(std::max<uint64_t>(db->n_seqs, 1u << 20), 1u << 26);
     return pl;
