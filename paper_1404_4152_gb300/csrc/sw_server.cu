@@ -100,8 +100,7 @@ struct sw_server {
     uint64_t* d_top_i = nullptr;
     int32_t* h_top_s = nullptr;    // pinned
     uint64_t* h_top_i = nullptr;
-    std::vector<uint32_t> slice_chunk0;  // slices + 1 chunk boundaries
-    uint64_t units = 0;
+    std::vector<uint32_t> slice_tile0;  // slices + 1 tile boundaries (multiples of 8)
 
     // statistics
     uint64_t waves = 0, completed = 0, rejected = 0, cells = 0;
@@ -128,67 +127,41 @@ void srv_release(sw_server* s) {
     if (s->stream) cudaStreamDestroy(s->stream);
 }
 
-// One wave: every active request advances by one slice.
-sw_status run_wave(sw_server* s, std::vector<std::shared_ptr<Request>>& act) {
+// Kernel launch over per-item chunk ranges of bin 1 (items = query pairs).
+sw_status launch_items(sw_server* s, KernelChoice kc, const std::vector<QueryPair>& items,
+                       const std::vector<uint32_t>& chunk0, const std::vector<uint32_t>& nchunk,
+                       int part) {
     sw_db* db = s->db;
     cudaError_t e;
-    // group by next slice; within a slice pair requests of similar length
-    std::vector<std::shared_ptr<Request>> order = act;
-    std::stable_sort(order.begin(), order.end(), [](const auto& x, const auto& y) {
-        if (x->next_slice != y->next_slice) return x->next_slice < y->next_slice;
-        return x->query.size() > y->query.size();
-    });
-    std::vector<QueryPair> pairs;
-    std::vector<uint32_t> prefix(1, 0), chunk0;
-    for (size_t i = 0; i < order.size();) {
-        const Request& a = *order[i];
-        QueryPair p{};
-        p.off_a = (uint64_t)a.slot * s->max_qlen;
-        p.len_a = (uint32_t)a.query.size();
-        p.q_a = (uint32_t)a.slot;
-        size_t used = 1;
-        if (i + 1 < order.size() && order[i + 1]->next_slice == a.next_slice) {
-            const Request& b = *order[i + 1];
-            p.off_b = (uint64_t)b.slot * s->max_qlen;
-            p.len_b = (uint32_t)b.query.size();
-            p.q_b = (uint32_t)b.slot;
-            used = 2;
-        } else {
-            p.off_b = p.off_a;
-            p.len_b = 0;
-            p.q_b = 0xffffffffu;
-        }
-        const uint32_t c0 = s->slice_chunk0[a.next_slice], c1 = s->slice_chunk0[a.next_slice + 1];
-        pairs.push_back(p);
-        chunk0.push_back(c0);
-        prefix.push_back(prefix.back() + (c1 - c0));
-        i += used;
-    }
-    const uint32_t np = (uint32_t)pairs.size();
-    if ((e = cudaMemcpyAsync(s->d_pairs, pairs.data(), np * sizeof(QueryPair),
-                             cudaMemcpyHostToDevice, s->stream)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(s->d_prefix, prefix.data(), (np + 1) * 4, cudaMemcpyHostToDevice,
+    const uint32_t n = (uint32_t)items.size();
+    if (n == 0) return SW_OK;
+    std::vector<uint32_t> prefix(n + 1, 0);
+    for (uint32_t i = 0; i < n; ++i) prefix[i + 1] = prefix[i] + nchunk[i];
+    QueryPair* d_pairs = s->d_pairs + (size_t)part * s->max_active;
+    uint32_t* d_prefix = s->d_prefix + (size_t)part * (s->max_active + 1);
+    uint32_t* d_chunk0 = s->d_chunk0 + (size_t)part * s->max_active;
+    uint32_t* counter = s->d_counters + 8 + part;
+    if ((e = cudaMemcpyAsync(d_pairs, items.data(), n * sizeof(QueryPair), cudaMemcpyHostToDevice,
                              s->stream)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(s->d_chunk0, chunk0.data(), np * 4, cudaMemcpyHostToDevice,
+        (e = cudaMemcpyAsync(d_prefix, prefix.data(), (n + 1) * 4, cudaMemcpyHostToDevice,
                              s->stream)) != cudaSuccess ||
-        (e = cudaMemsetAsync(s->d_counters, 0, 64, s->stream)) != cudaSuccess)
+        (e = cudaMemcpyAsync(d_chunk0, chunk0.data(), n * 4, cudaMemcpyHostToDevice,
+                             s->stream)) != cudaSuccess)
         return cuda_fail(e, "server: wave upload");
-
-    const bool i32 = (int64_t)s->scheme_alpha + s->scheme_beta > 32768;
     WavefrontArgs a{};
     a.tile_data = db->d_tile_data;
     a.tile_off = db->d_tile_off;
     a.tile_len = db->d_tile_len;
     a.sorted_ids = db->d_sorted;
     a.bin[1].first_unit = 0;
-    a.bin[1].n_units = s->units;
+    a.bin[1].n_units = db->n_tiles * (kc.mode == KernelChoice::kPairDb ? kTilePairs : kTileSeqs);
     a.bin[1].boundary = s->d_bnd;
     a.bin[1].bstride = s->bstride;
     a.query = s->d_queries;
-    a.pairs = s->d_pairs;
-    a.n_pairs = np;
-    a.item_prefix = s->d_prefix;
-    a.pair_chunk0 = s->d_chunk0;
+    a.pairs = d_pairs;
+    a.n_pairs = n;
+    a.item_prefix = d_prefix;
+    a.pair_chunk0 = d_chunk0;
     a.matrix = s->d_matrix;
     a.alphabet = db->alphabet;
     a.alpha = s->scheme_alpha;
@@ -198,38 +171,84 @@ sw_status run_wave(sw_server* s, std::vector<std::shared_ptr<Request>>& act) {
     a.flag_list = s->d_flags;
     a.flag_count = s->d_counters + 3;
     a.flag_cap = s->flag_cap;
-    a.work_counter = s->d_counters + 0;
-    // int32 lanes hold one query: give every request its own item
-    std::vector<QueryPair> singles;
-    if (i32) {
-        std::vector<uint32_t> pre(1, 0), c0s;
-        for (auto& r : order) {
-            QueryPair p{};
-            p.off_a = p.off_b = (uint64_t)r->slot * s->max_qlen;
-            p.len_a = (uint32_t)r->query.size();
-            p.q_a = (uint32_t)r->slot;
-            p.q_b = 0xffffffffu;
-            singles.push_back(p);
-            const uint32_t c0 = s->slice_chunk0[r->next_slice], c1 = s->slice_chunk0[r->next_slice + 1];
-            c0s.push_back(c0);
-            pre.push_back(pre.back() + (c1 - c0));
-        }
-        a.n_pairs = (uint32_t)singles.size();
-        if ((e = cudaMemcpyAsync(s->d_pairs, singles.data(), singles.size() * sizeof(QueryPair),
-                                 cudaMemcpyHostToDevice, s->stream)) != cudaSuccess ||
-            (e = cudaMemcpyAsync(s->d_prefix, pre.data(), pre.size() * 4, cudaMemcpyHostToDevice,
-                                 s->stream)) != cudaSuccess ||
-            (e = cudaMemcpyAsync(s->d_chunk0, c0s.data(), c0s.size() * 4, cudaMemcpyHostToDevice,
-                                 s->stream)) != cudaSuccess)
-            return cuda_fail(e, "server: wave upload");
-    }
-    const KernelChoice kc = i32 ? KernelChoice{KernelChoice::kInt32, 16}
-                                : KernelChoice{KernelChoice::kQueryPair, 16};
+    a.work_counter = counter;
     const int occ = std::max(1, wavefront_occupancy(kc, nullptr));
     const int grid = std::max(1, std::min(s->grid, db->nsm * occ));
     if ((e = launch_wavefront(kc, a, grid, s->stream)) != cudaSuccess)
         return cuda_fail(e, "server: wave kernel");
     db->launches += 1;
+    return SW_OK;
+}
+
+// One wave: every active request advances by one slice. Requests at the same
+// slice are paired (two queries per 16-bit lane pair); one left over at a
+// slice runs alone in the mode that packs two database sequences instead.
+sw_status run_wave(sw_server* s, std::vector<std::shared_ptr<Request>>& act) {
+    sw_db* db = s->db;
+    cudaError_t e;
+    std::vector<std::shared_ptr<Request>> order = act;
+    std::stable_sort(order.begin(), order.end(), [](const auto& x, const auto& y) {
+        if (x->next_slice != y->next_slice) return x->next_slice < y->next_slice;
+        return x->query.size() > y->query.size();
+    });
+    const bool i32 = (int64_t)s->scheme_alpha + s->scheme_beta > 32768;
+    auto one = [&](const Request& r) {
+        QueryPair p{};
+        p.off_a = p.off_b = (uint64_t)r.slot * s->max_qlen;
+        p.len_a = (uint32_t)r.query.size();
+        p.q_a = (uint32_t)r.slot;
+        p.q_b = 0xffffffffu;
+        return p;
+    };
+    // chunk ranges of a slice: 4-tile chunks (one sequence per unit), 8-tile chunks (pairs)
+    auto range4 = [&](uint32_t sl, uint32_t* c0, uint32_t* n) {
+        const uint32_t t0 = s->slice_tile0[sl], t1 = s->slice_tile0[sl + 1];
+        *c0 = t0 / 4;
+        *n = (t1 + 3) / 4 - t0 / 4;
+    };
+    auto range8 = [&](uint32_t sl, uint32_t* c0, uint32_t* n) {
+        const uint32_t t0 = s->slice_tile0[sl], t1 = s->slice_tile0[sl + 1];
+        *c0 = t0 / 8;
+        *n = (t1 + 7) / 8 - t0 / 8;
+    };
+    if ((e = cudaMemsetAsync(s->d_counters, 0, 64, s->stream)) != cudaSuccess)
+        return cuda_fail(e, "server: counter reset");
+    std::vector<QueryPair> pairs, singles;
+    std::vector<uint32_t> pc0, pn, sc0, sn;
+    for (size_t i = 0; i < order.size();) {
+        const Request& ra = *order[i];
+        uint32_t c0, n;
+        if (i32) {
+            singles.push_back(one(ra));
+            range4(ra.next_slice, &c0, &n);
+            sc0.push_back(c0);
+            sn.push_back(n);
+            i += 1;
+        } else if (i + 1 < order.size() && order[i + 1]->next_slice == ra.next_slice) {
+            const Request& rb = *order[i + 1];
+            QueryPair p = one(ra);
+            p.off_b = (uint64_t)rb.slot * s->max_qlen;
+            p.len_b = (uint32_t)rb.query.size();
+            p.q_b = (uint32_t)rb.slot;
+            pairs.push_back(p);
+            range4(ra.next_slice, &c0, &n);
+            pc0.push_back(c0);
+            pn.push_back(n);
+            i += 2;
+        } else {
+            singles.push_back(one(ra));
+            range8(ra.next_slice, &c0, &n);
+            sc0.push_back(c0);
+            sn.push_back(n);
+            i += 1;
+        }
+    }
+    sw_status st;
+    if ((st = launch_items(s, KernelChoice{KernelChoice::kQueryPair, 16}, pairs, pc0, pn, 0)))
+        return st;
+    const KernelChoice ks = i32 ? KernelChoice{KernelChoice::kInt32, 16}
+                                : KernelChoice{KernelChoice::kPairDb, 16};
+    if ((st = launch_items(s, ks, singles, sc0, sn, 1))) return st;
     if (!i32) {
         RescoreArgs r{};
         r.tile_data = db->d_tile_data;
@@ -396,35 +415,32 @@ extern "C" sw_status sw_server_create(sw_db* db, const sw_server_opts* opts, sw_
                         (unsigned long long)budget, (unsigned long long)slot_bytes);
         s->max_active = (uint32_t)std::min<uint64_t>(s->max_active, fit);
     }
-    const uint64_t chunk_units = (uint64_t)wavefront_short_units_per_chunk();
-    s->units = db->n_tiles * kTileSeqs;
-    const uint64_t n_chunks = (s->units + chunk_units - 1) / chunk_units;
-    s->slices = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(s->slices, n_chunks));
-    // slices of about equal work (padded tile residues), in chunk units
+    // slices of about equal work (padded tile residues), cut at multiples of 8 tiles
     {
-        std::vector<uint64_t> work(n_chunks, 0);
-        for (uint64_t t = 0; t < db->n_tiles; ++t)
-            work[(t * kTileSeqs) / chunk_units] += (uint64_t)db->tile_len_host[t] * kTileSeqs;
+        const uint64_t groups = (db->n_tiles + 7) / 8;
+        s->slices = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(s->slices, groups));
+        std::vector<uint64_t> work(groups, 0);
         uint64_t total = 0;
-        for (auto w : work) total += w;
-        s->slice_chunk0.assign(1, 0);
+        for (uint64_t t = 0; t < db->n_tiles; ++t) {
+            work[t / 8] += (uint64_t)db->tile_len_host[t] * kTileSeqs;
+            total += (uint64_t)db->tile_len_host[t] * kTileSeqs;
+        }
+        std::vector<uint32_t> b(1, 0);
         uint64_t acc = 0;
         uint32_t k = 1;
-        for (uint64_t c = 0; c < n_chunks && k < s->slices; ++c) {
-            acc += work[c];
+        for (uint64_t g = 0; g < groups && k < s->slices; ++g) {
+            acc += work[g];
             if (acc * s->slices >= total * k) {
-                s->slice_chunk0.push_back((uint32_t)(c + 1));
+                if ((g + 1) * 8 < db->n_tiles) b.push_back((uint32_t)((g + 1) * 8));
                 ++k;
             }
         }
-        while (s->slice_chunk0.size() < (size_t)s->slices) s->slice_chunk0.push_back((uint32_t)n_chunks);
-        s->slice_chunk0.push_back((uint32_t)n_chunks);
-        // drop empty slices
-        std::vector<uint32_t> b(1, 0);
-        for (size_t i = 1; i < s->slice_chunk0.size(); ++i)
-            if (s->slice_chunk0[i] > b.back()) b.push_back(s->slice_chunk0[i]);
-        s->slice_chunk0 = b;
-        s->slices = (uint32_t)b.size() - 1;
+        b.push_back((uint32_t)db->n_tiles);
+        std::vector<uint32_t> u(1, 0);
+        for (size_t i = 1; i < b.size(); ++i)
+            if (b[i] > u.back()) u.push_back(b[i]);
+        s->slice_tile0 = u;
+        s->slices = (uint32_t)u.size() - 1;
     }
     cudaError_t e;
     const KernelChoice kqp{KernelChoice::kQueryPair, 16}, ki32{KernelChoice::kInt32, 16};
@@ -440,10 +456,10 @@ extern "C" sw_status sw_server_create(sw_db* db, const sw_server_opts* opts, sw_
         (e = srv_alloc(s.get(), (void**)&s->d_queries, (size_t)A * s->max_qlen)) != cudaSuccess ||
         (e = srv_alloc(s.get(), (void**)&s->d_matrix, SW_MAX_ALPHABET * SW_MAX_ALPHABET)) !=
             cudaSuccess ||
-        (e = srv_alloc(s.get(), (void**)&s->d_pairs, (size_t)A * sizeof(QueryPair))) !=
+        (e = srv_alloc(s.get(), (void**)&s->d_pairs, (size_t)2 * A * sizeof(QueryPair))) !=
             cudaSuccess ||
-        (e = srv_alloc(s.get(), (void**)&s->d_prefix, (size_t)(A + 1) * 4)) != cudaSuccess ||
-        (e = srv_alloc(s.get(), (void**)&s->d_chunk0, (size_t)A * 4)) != cudaSuccess ||
+        (e = srv_alloc(s.get(), (void**)&s->d_prefix, (size_t)2 * (A + 1) * 4)) != cudaSuccess ||
+        (e = srv_alloc(s.get(), (void**)&s->d_chunk0, (size_t)2 * A * 4)) != cudaSuccess ||
         (e = srv_alloc(s.get(), (void**)&s->d_qoff, (size_t)A * 8)) != cudaSuccess ||
         (e = srv_alloc(s.get(), (void**)&s->d_qlen, (size_t)A * 4)) != cudaSuccess ||
         (e = srv_alloc(s.get(), (void**)&s->d_flags, (size_t)s->flag_cap * sizeof(uint2))) !=

@@ -1,0 +1,55 @@
+"""Full-size workloads in the configuration the benchmark runs, checked on sampled outputs.
+
+At these sizes the oracle cannot score every pair in a test's time, so each
+test checks (a) a seeded random sample of scores and every top-k hit against
+the oracle one by one, and (b) that the returned top-k list is exactly the
+ranked top-k of the returned score vector.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests import pins
+
+pytestmark = pytest.mark.gpu
+
+sw = pytest.importorskip("paper_1404_4152_gb300")
+
+
+def _check_sampled(w, q, scores, ts, ti, sample, extra=()):
+    rng = np.random.default_rng(7)
+    idx = np.unique(np.concatenate([rng.integers(0, w.n_seqs, size=sample), ti.astype(np.int64),
+                                    np.asarray(extra, dtype=np.int64)]))
+    es = oracle.scores(q, w.residues, w.offsets, w.matrix, w.alpha, w.beta, which=idx)
+    bad = np.nonzero(scores[idx] != es)[0]
+    assert bad.size == 0, (idx[bad[:8]], scores[idx[bad[:8]]], es[bad[:8]])
+    ets, eti = pins.ranked_top_k(scores, w.top_k)
+    assert np.array_equal(ts, ets) and np.array_equal(ti, eti)
+
+
+def test_two_million_sequences_sampled():
+    w = synth.config1()
+    with sw.sw_db_load(w.residues, w.offsets) as db:
+        for q in (w.queries[0], w.queries[10], w.queries[19]):
+            scores, ts, ti, st = sw.sw_search(db, q, w.matrix, w.alpha, w.beta, w.top_k)
+            _check_sampled(w, q, scores, ts, ti, sample=400 if q.size > 2000 else 1500)
+
+
+@pytest.mark.parametrize("scale", [1, 3])
+def test_long_sequences_and_planted_duplicates(scale):
+    """A 5,478-residue query against 100,000 sequences of mean length 2,000 (up to 35,000),
+    1,000 of them near-copies of the query. scale 3 multiplies the matrix and penalties by 3,
+    which pushes the planted pairs past the 16-bit range and through int32 rescoring."""
+    w = synth.config4(scale=scale)
+    q = w.queries[0]
+    planted = w.notes["planted"]
+    with sw.sw_db_load(w.residues, w.offsets, long_threshold=3000) as db:
+        assert db.info()["n_long"] > 10000
+        scores, ts, ti, st = sw.sw_search(db, q, w.matrix, w.alpha, w.beta, w.top_k)
+        assert (st["recomputed"] > 0) == (scale > 1)
+        _check_sampled(w, q, scores, ts, ti, sample=120, extra=planted[:200])
+        # every top hit is a planted near-duplicate
+        assert set(ti.tolist()) <= set(int(p) for p in planted)
+        if scale > 1:
+            assert scores[planted].min() > 32767
