@@ -47,6 +47,11 @@ ALU_OPS_PER_CELL = 3.5
 ALU_LANES_PER_CLK_SM = 64     # 32-bit lanes per clock per SM on the integer ALU pipe (4 x 16)
 S16X2_CELLS_PER_LANE = 2      # one 32-bit lane holds two 16-bit DP cells
 PAPER_PHI_GCUPS_MAX = 58.8    # SWAPHI InterSP, one Xeon Phi 5110P, TrEMBL (Section IV.A)
+# DRAM bytes per DP cell of the search kernel (ncu dram__bytes_read + _write on a
+# 600,000-sequence case; profiles/search_kernel_pairdb_600k_ncu.md), valid for the
+# kernel source whose sha256 starts with TRAFFIC_SOURCE.
+TRAFFIC_BYTES_PER_CELL = 0.0277
+TRAFFIC_SOURCE = "10a819ec0d0d5ef1"
 
 
 def parse_args():
@@ -407,15 +412,11 @@ def run_ours(args):
     nsm = props.multi_processor_count
     sm_mhz = clocks["sm_mhz"] if clocks else 2070.0
     peak = nsm * sm_mhz * 1e6 * ALU_LANES_PER_CLK_SM * S16X2_CELLS_PER_LANE / 1e9
-    traffic = None
-    tfile = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tfile):
-        try:
-            tj = json.load(open(tfile))
-            if tj.get("kernel") == dom and tj.get("bytes_per_cell"):
-                traffic = tj["bytes_per_cell"] * cells_per_launch
-        except Exception:
-            traffic = None
+    import hashlib
+
+    src = os.path.join(ROOT, "paper_1404_4152_gb300", "csrc", "sw_wavefront.cu")
+    same_kernel = hashlib.sha256(open(src, "rb").read()).hexdigest().startswith(TRAFFIC_SOURCE)
+    traffic = TRAFFIC_BYTES_PER_CELL * cells_per_launch if same_kernel else None
     roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "Gop/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "per_unit": f"{ALU_OPS_PER_CELL} integer ALU lane-ops per DP cell (minimum); "
