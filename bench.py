@@ -383,8 +383,16 @@ def run_ours(args):
     prof = sw.sw_db_get_profile(db)
 
     t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    merged = None
     if world > 1:
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        # the one exchange of a sharded search: every rank's top-k (global indices) merged
+        from paper_1404_4152_gb300 import shard
+
+        last = len(qlens) - 1
+        ms_, mi_ = shard.allgather_top_k(d_ts[last].cpu().numpy(),
+                                         d_ti[last].cpu().numpy().astype(np.uint64) + rank * n, k)
+        merged = {"query": last, "top_scores": ms_.tolist()[:3], "top_index": mi_.tolist()[:3]}
     ms_max = float(t.item())
     cells_rank = sum(qlens) * w.db_residues * args.steps
     cells_all = cells_rank * world
@@ -483,6 +491,7 @@ def run_ours(args):
         "phases_ms": {p: ph[p]["ms"] for p in ph},
         "batched": batched,
         "served": served,
+        "sharded_top_k": merged,
         "tuning": tuning,
         "per_query": per_query,
         "context": {"paper_xeon_phi_gcups_max": PAPER_PHI_GCUPS_MAX},

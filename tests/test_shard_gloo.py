@@ -1,0 +1,88 @@
+"""The multi-GPU shard plan on CPU ranks: partition balance and the top-k exchange.
+
+Two gloo processes each score their shard with the oracle (standing in for a
+GPU) and exchange their local top-k with one all-gather; the merged list must
+equal the single-process top-k of the whole database.
+"""
+import os
+import socket
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from paper_1404_4152_gb300 import shard
+from tests import pins
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def test_partition_balances_residues_and_covers_everything():
+    lengths = synth.gen_lengths(5000, synth.db_qtable(), 501, 1)
+    off = np.zeros(lengths.size + 1, np.uint64)
+    off[1:] = np.cumsum(lengths)
+    for world in (2, 3, 4, 8):
+        parts = shard.partition(off, world)
+        allidx = np.sort(np.concatenate(parts))
+        assert np.array_equal(allidx, np.arange(lengths.size))
+        loads = [int(lengths[p].sum()) for p in parts]
+        assert max(loads) - min(loads) <= int(lengths.max())
+
+
+def test_merge_matches_global_ranking_with_ties():
+    rng = np.random.default_rng(5)
+    scores = rng.integers(0, 6, size=300).astype(np.int32)  # heavy ties
+    parts = shard.partition(np.concatenate([[0], np.cumsum(rng.integers(1, 9, size=300))]), 3)
+    local = []
+    for p in parts:
+        ts, ti = pins.ranked_top_k(scores[p], 12)
+        local.append((ts, p[ti.astype(np.int64)].astype(np.uint64)))
+    ms, mi = shard.merge_top_k(local, 12)
+    es, ei = pins.ranked_top_k(scores, 12)
+    assert np.array_equal(ms, es) and np.array_equal(mi, ei)
+
+
+def _worker(rank, world, port, q):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    w = synth.config0()
+    n = 1200
+    off = w.offsets[: n + 1]
+    res = w.residues[: int(off[-1])]
+    gi = shard.partition(off, world)[rank]
+    sres, soff = shard.shard_arrays(res, off, gi)
+    local = oracle.scores(w.queries[0], sres, soff, w.matrix, w.alpha, w.beta)
+    ts, ti = pins.ranked_top_k(local, 10)
+    ms, mi = shard.allgather_top_k(ts, gi[ti.astype(np.int64)], 10)
+    q.put((rank, ms.tolist(), mi.tolist()))
+    dist.destroy_process_group()
+
+
+def test_two_rank_allgather_top_k():
+    import torch.multiprocessing as mp
+
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = [q.get(timeout=120) for _ in procs]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    w = synth.config0()
+    off = w.offsets[:1201]
+    full = oracle.scores(w.queries[0], w.residues[: int(off[-1])], off, w.matrix, w.alpha, w.beta)
+    es, ei = pins.ranked_top_k(full, 10)
+    for rank, ms, mi in out:
+        assert ms == es.tolist() and mi == ei.tolist(), rank
