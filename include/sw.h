@@ -72,6 +72,8 @@ typedef struct {
 
 #define SW_DB_FLAG_FORCE_INT32 1u   /* skip the packed 16-bit kernels; everything in int32 */
 #define SW_DB_FLAG_PROFILE 2u       /* time every kernel phase with CUDA events (sw_db_get_profile) */
+#define SW_DB_FLAG_QUERY_PROFILE 4u /* single queries use the int8 query-profile kernel instead of
+                                       the score-profile ring (Section III.B.2 compares the two) */
 
 typedef struct sw_db sw_db;
 
@@ -214,18 +216,21 @@ sw_status sw_search_batch_device(sw_db* db, uint32_t nq, const uint8_t* d_querie
  * Autotuning (no counterpart in the paper, which fixes its kernel shapes; the
  * score-profile width N = 8 of Section III.B.3 is the nearest analogue).
  * Times the search kernel on a sample of this database for every kernel mode
- * (index 0: one query against pairs of database sequences; 1: two queries per
- * lane pair, used by batches and the server; 2: int32) and every rows-per-lane
+ * (index 0: one query against pairs of database sequences, int8 query profile;
+ * 1: two queries per lane pair, used by batches and the server; 2: int32;
+ * 3: one query against pairs with the score-profile ring of Section III.B.2,
+ * the default for single queries) and every rows-per-lane
  * choice R in {8, 12, 16, 20, 24}, and stores the device time per query row
  * and database residue. Later searches on the handle pick R by minimising
- * padded rows x measured cost. int32_over_int16 is the measured speed ratio;
+ * padded rows x measured cost, and single queries take the faster of modes 0
+ * and 3. int32_over_int16 is the measured speed ratio;
  * cutover_fraction the share of saturating pairs above which a search would be
  * cheaper in int32 (the 16/32-bit cutover). cache_path (may be NULL) names a
  * JSON file reused when its GPU name and SM count match.
  */
 typedef struct {
-    double ns_per_row_residue[3][5];
-    uint32_t fastest_R[3];
+    double ns_per_row_residue[4][5];
+    uint32_t fastest_R[4];
     double int32_over_int16;
     double cutover_fraction;
     int from_cache;

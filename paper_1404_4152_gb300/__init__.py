@@ -29,6 +29,7 @@ SW_MAX_ALPHABET = 32
 SW_MAX_TOP_K = 1024
 SW_DB_FLAG_FORCE_INT32 = 1
 SW_DB_FLAG_PROFILE = 2
+SW_DB_FLAG_QUERY_PROFILE = 4
 PHASES = ("wavefront", "rescore_int32", "topk", "batch")
 
 _STATUS = {0: "SW_OK", 1: "SW_ERR_INVALID_ARG", 2: "SW_ERR_OOM", 3: "SW_ERR_CUDA",
@@ -86,8 +87,8 @@ class sw_server_stats(ctypes.Structure):
 
 
 class sw_tuning(ctypes.Structure):
-    _fields_ = [("ns_per_row_residue", (ctypes.c_double * 5) * 3),
-                ("fastest_R", ctypes.c_uint32 * 3), ("int32_over_int16", ctypes.c_double),
+    _fields_ = [("ns_per_row_residue", (ctypes.c_double * 5) * 4),
+                ("fastest_R", ctypes.c_uint32 * 4), ("int32_over_int16", ctypes.c_double),
                 ("cutover_fraction", ctypes.c_double), ("from_cache", ctypes.c_int)]
 
 
@@ -404,10 +405,10 @@ def sw_db_autotune(db: Database, matrix, alpha: int, beta: int, cache_path: str 
     _check(load_library().sw_db_autotune(db.handle, _ptr(m), int(alpha), int(beta),
                                          cache_path.encode() if cache_path else None,
                                          ctypes.byref(t)))
-    modes = ("pair_db", "query_pair", "int32")
-    return {"ns_per_row_residue": {modes[i]: list(t.ns_per_row_residue[i]) for i in range(3)},
+    modes = ("pair_db", "query_pair", "int32", "pair_ring")
+    return {"ns_per_row_residue": {modes[i]: list(t.ns_per_row_residue[i]) for i in range(4)},
             "rows_per_lane": [8, 12, 16, 20, 24],
-            "fastest_R": {modes[i]: t.fastest_R[i] for i in range(3)},
+            "fastest_R": {modes[i]: t.fastest_R[i] for i in range(4)},
             "int32_over_int16": t.int32_over_int16, "cutover_fraction": t.cutover_fraction,
             "from_cache": bool(t.from_cache)}
 

@@ -77,10 +77,19 @@ struct WavefrontArgs {
 };
 
 struct KernelChoice {
-    enum Mode { kPairDb = 0, kQueryPair = 1, kInt32 = 2 };
+    // kPairRing: one query against pairs like kPairDb, with the score-profile ring
+    enum Mode { kPairDb = 0, kQueryPair = 1, kInt32 = 2, kPairRing = 3 };
     Mode mode;    // what the two 16-bit halves hold (or int32 lanes)
     int R;        // query rows per thread in the short bin
 };
+constexpr int kModes = 4;
+
+// Work units per database tile: pairs of sequences for the single-query
+// packed kernels, sequences otherwise.
+inline uint32_t units_per_tile(const KernelChoice& kc) {
+    return kc.mode == KernelChoice::kPairDb || kc.mode == KernelChoice::kPairRing ? kTilePairs
+                                                                                 : kTileSeqs;
+}
 
 // Arguments of the int32 rescoring kernel (a list of (query row, sorted position)).
 struct RescoreArgs {

@@ -56,9 +56,20 @@ bool use_int32(const sw_db* db, int32_t alpha, int32_t beta) {
     return (db->flags & SW_DB_FLAG_FORCE_INT32) || (int64_t)alpha + beta > 32768;
 }
 
+// One query against pairs of database sequences: the score-profile ring
+// unless the autotuner measured the int8 query profile faster on this GPU.
 KernelChoice single_choice(const sw_db* db, uint32_t qlen, bool i32) {
     if (i32) return KernelChoice{KernelChoice::kInt32, 16};
-    return KernelChoice{KernelChoice::kPairDb, choose_R(db, 0, {qlen}, 4.5)};
+    const KernelChoice qp{KernelChoice::kPairDb, choose_R(db, 0, {qlen}, 4.5)};
+    if (db->flags & SW_DB_FLAG_QUERY_PROFILE) return qp;
+    const KernelChoice ring{KernelChoice::kPairRing, choose_R(db, 3, {qlen}, 3.9)};
+    if (!db->tuned) return ring;
+    auto cost = [&](const KernelChoice& k) {
+        const uint32_t TR = (uint32_t)kShortT * k.R;
+        const int i = (k.R - 8) / 4;
+        return (double)((qlen + TR - 1) / TR) * TR * db->tuning.ns_per_row_residue[k.mode][i];
+    };
+    return cost(qp) < cost(ring) ? qp : ring;
 }
 
 // Two halves per slot, each the longest unit plus the wavefront's slack.
@@ -78,6 +89,7 @@ std::vector<KernelChoice> all_choices() {
     for (int R : kShortR) {
         v.push_back(KernelChoice{KernelChoice::kPairDb, R});
         v.push_back(KernelChoice{KernelChoice::kQueryPair, R});
+        v.push_back(KernelChoice{KernelChoice::kPairRing, R});
     }
     v.push_back(KernelChoice{KernelChoice::kInt32, 16});
     return v;
@@ -279,7 +291,7 @@ sw_status enqueue_search(sw_db* db, const uint8_t* d_query, uint32_t qlen, const
     const KernelChoice kc = single_choice(db, qlen, i32);
     {
         WavefrontArgs a = base_args(db, d_matrix, alpha, beta, d_scores, db->n_seqs,
-                                    kc.mode == KernelChoice::kPairDb ? kTilePairs : kTileSeqs);
+                                    units_per_tile(kc));
         a.query = d_query;
         a.qlen = qlen;
         a.flag_list = db->d_flags2;

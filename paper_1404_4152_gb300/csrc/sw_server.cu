@@ -154,7 +154,7 @@ sw_status launch_items(sw_server* s, KernelChoice kc, const std::vector<QueryPai
     a.tile_len = db->d_tile_len;
     a.sorted_ids = db->d_sorted;
     a.bin[1].first_unit = 0;
-    a.bin[1].n_units = db->n_tiles * (kc.mode == KernelChoice::kPairDb ? kTilePairs : kTileSeqs);
+    a.bin[1].n_units = db->n_tiles * (units_per_tile(kc));
     a.bin[1].boundary = s->d_bnd;
     a.bin[1].bstride = s->bstride;
     a.query = s->d_queries;
@@ -247,7 +247,9 @@ sw_status run_wave(sw_server* s, std::vector<std::shared_ptr<Request>>& act) {
     if ((st = launch_items(s, KernelChoice{KernelChoice::kQueryPair, 16}, pairs, pc0, pn, 0)))
         return st;
     const KernelChoice ks = i32 ? KernelChoice{KernelChoice::kInt32, 16}
-                                : KernelChoice{KernelChoice::kPairDb, 16};
+                          : KernelChoice{(db->flags & SW_DB_FLAG_QUERY_PROFILE) ? KernelChoice::kPairDb
+                                                                                : KernelChoice::kPairRing,
+                                         16};
     if ((st = launch_items(s, ks, singles, sc0, sn, 1))) return st;
     if (!i32) {
         RescoreArgs r{};
@@ -443,9 +445,11 @@ extern "C" sw_status sw_server_create(sw_db* db, const sw_server_opts* opts, sw_
         s->slices = (uint32_t)u.size() - 1;
     }
     cudaError_t e;
-    const KernelChoice kqp{KernelChoice::kQueryPair, 16}, ki32{KernelChoice::kInt32, 16};
-    s->grid = db->nsm * std::max(1, std::max(wavefront_occupancy(kqp, nullptr),
-                                             wavefront_occupancy(ki32, nullptr)));
+    const KernelChoice kqp{KernelChoice::kQueryPair, 16}, ki32{KernelChoice::kInt32, 16},
+        kring{KernelChoice::kPairRing, 16};
+    s->grid = db->nsm * std::max(1, std::max({wavefront_occupancy(kqp, nullptr),
+                                              wavefront_occupancy(ki32, nullptr),
+                                              wavefront_occupancy(kring, nullptr)}));
     s->bstride = 2ull * (((uint64_t)std::max(4u, (db->max_len + 3u) & ~3u) + boundary_slack() + 3) &
                          ~3ull);
     s->flag_cap = (uint32_t)std::min<uint64_t>(std::max<uint64_t>(db->n_seqs, 1u << 20), 1u << 26);

@@ -1,7 +1,8 @@
 // Autotuner: measured kernel shapes for one database on this GPU.
 //
-// For every kernel mode (one query against database pairs, two queries per
-// lane pair, int32) and every rows-per-lane choice R, the tuner times the
+// For every kernel mode (one query against database pairs with the int8
+// query profile, two queries per lane pair, int32, one query against pairs
+// with the score-profile ring) and every rows-per-lane choice R, the tuner times the
 // search kernel on a sample of the database's shorter sequences with a query
 // whose length fills whole passes, and records the device time per query row
 // and database residue. The search paths then pick R per query (or batch) by
@@ -31,7 +32,7 @@ const int kR[kTuneR] = {8, 12, 16, 20, 24};
 std::string gpu_key(int device) {
     cudaDeviceProp p;
     cudaGetDeviceProperties(&p, device);
-    char buf[256];
+    char buf[320];
     snprintf(buf, sizeof buf, "%s|sm=%d", p.name, p.multiProcessorCount);
     return buf;
 }
@@ -61,7 +62,8 @@ bool load_cache(const char* path, const std::string& key, sw_tuning* t) {
     };
     return read_row("pair_db", t->ns_per_row_residue[0], kTuneR) &&
            read_row("query_pair", t->ns_per_row_residue[1], kTuneR) &&
-           read_row("int32", t->ns_per_row_residue[2], kTuneR);
+           read_row("int32", t->ns_per_row_residue[2], kTuneR) &&
+           read_row("pair_ring", t->ns_per_row_residue[3], kTuneR);
 }
 
 void save_cache(const char* path, const std::string& key, const sw_tuning* t) {
@@ -69,12 +71,12 @@ void save_cache(const char* path, const std::string& key, const sw_tuning* t) {
     FILE* f = fopen(path, "w");
     if (!f) return;
     fprintf(f, "{\n  \"gpu\": \"%s\",\n  \"rows_per_lane\": [8, 12, 16, 20, 24],\n", key.c_str());
-    const char* names[3] = {"pair_db", "query_pair", "int32"};
-    for (int m = 0; m < 3; ++m) {
+    const char* names[kModes] = {"pair_db", "query_pair", "int32", "pair_ring"};
+    for (int m = 0; m < kModes; ++m) {
         fprintf(f, "  \"%s\": [", names[m]);
         for (int i = 0; i < kTuneR; ++i)
             fprintf(f, "%.6g%s", t->ns_per_row_residue[m][i], i + 1 < kTuneR ? ", " : "");
-        fprintf(f, "]%s\n", m < 2 ? "," : "");
+        fprintf(f, "]%s\n", m + 1 < kModes ? "," : "");
     }
     fprintf(f, "}\n");
     fclose(f);
@@ -118,7 +120,7 @@ extern "C" sw_status sw_db_autotune(sw_db* db, const int8_t* matrix, int32_t alp
         cudaEvent_t e0, e1;
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
-        for (int mode = 0; mode < 3; ++mode) {
+        for (int mode = 0; mode < kModes; ++mode) {
             for (int i = 0; i < kTuneR; ++i) {
                 const int R = kR[i];
                 const KernelChoice kc{(KernelChoice::Mode)mode, R};
@@ -144,7 +146,7 @@ extern "C" sw_status sw_db_autotune(sw_db* db, const int8_t* matrix, int32_t alp
                 a.qlen = qlen;
                 a.bin[1].boundary = db->d_bnd_short;
                 a.bin[1].bstride = db->bstride_short;
-                const uint64_t per = (mode == KernelChoice::kPairDb) ? 2 : 1;
+                const uint64_t per = units_per_tile(kc) == kTilePairs ? 2 : 1;
                 a.bin[1].first_unit = first / per;
                 a.bin[1].n_units = sample / per;
                 if (mode == KernelChoice::kQueryPair) {
@@ -187,11 +189,15 @@ extern "C" sw_status sw_db_autotune(sw_db* db, const int8_t* matrix, int32_t alp
     }
     // the 16/32-bit cutover: int32 wins when more than this fraction of pairs would be
     // rescored (rescoring redoes a pair in int32 after its 16-bit pass)
-    const double c16 = t.ns_per_row_residue[0][2], c32 = t.ns_per_row_residue[2][2];
+    // (16-bit: the faster of the two single-query modes at R = 16)
+    double c16 = t.ns_per_row_residue[0][2];
+    const double ring16 = t.ns_per_row_residue[3][2];
+    if (ring16 > 0 && (c16 <= 0 || ring16 < c16)) c16 = ring16;
+    const double c32 = t.ns_per_row_residue[2][2];
     t.int32_over_int16 = c16 > 0 ? c32 / c16 : 0;
     t.cutover_fraction = c32 > 0 ? std::max(0.0, 1.0 - c16 / c32) : 0;
     t.from_cache = cached ? 1 : 0;
-    for (int m = 0; m < 3; ++m) {
+    for (int m = 0; m < kModes; ++m) {
         int bi = 0;
         for (int i = 0; i < kTuneR; ++i)
             if (t.ns_per_row_residue[m][i] > 0 &&

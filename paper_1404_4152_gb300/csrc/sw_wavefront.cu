@@ -50,6 +50,9 @@ namespace {
 
 constexpr int kWarps = 8;
 constexpr int kThreads = kWarps * 32;
+// Columns between consecutive threads of a group in process_chunk: thread t
+// works on column s - kSkew * t at step s.
+constexpr int kSkew = 2;
 
 // fsbt(q[row], r) for one query row, 0 outside the query or the alphabet.
 __device__ __forceinline__ int profile_score(const uint8_t* q, uint32_t qlen, const int8_t* matrix,
@@ -102,6 +105,7 @@ struct ItemQuery {
 struct ModePairDb {
     using Lane = LaneS16x2;
     static constexpr bool kPairStream = true;  // both sequences of the tile pair
+    static constexpr bool kRing = false;
     template <int T, int R>
     struct Prof {
         static constexpr int TR = T * R;
@@ -152,6 +156,7 @@ __device__ __forceinline__ void load_chunks(const uint8_t* prof, uint32_t code, 
 struct ModeQueryPair {
     using Lane = LaneS16x2;
     static constexpr bool kPairStream = false;
+    static constexpr bool kRing = false;
     template <int T, int R>
     struct Prof {
         static constexpr int TR = T * R;
@@ -189,6 +194,7 @@ struct ModeQueryPair {
 struct ModeInt32 {
     using Lane = LaneS32;
     static constexpr bool kPairStream = false;
+    static constexpr bool kRing = false;
     template <int T, int R>
     struct Prof {
         static constexpr int TR = T * R;
@@ -221,8 +227,8 @@ struct ModeInt32 {
 // item's query (pair). All warps of the block process the same chunk, pass by
 // pass.
 //
-// Boundary rows: entry T + j of a slot half holds (H, E) of column j (entries
-// below T take the fill steps' writes and are never read). Thread 0 reads them
+// Boundary rows: entry kSkew T + j of a slot half holds (H, E) of column j
+// (entries below kSkew T take the fill steps' writes and are never read). Thread 0 reads them
 // in aligned 4-column blocks; blocks at or past the unit's length L (a
 // multiple of 4) read as zero, which is safe for the pad columns there: every
 // value they produce stays at or below the largest real H.
@@ -269,7 +275,7 @@ __device__ __forceinline__ void process_chunk(const WavefrontArgs& a, const BinA
     uint32_t Lw = L;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) Lw = max(Lw, __shfl_xor_sync(0xffffffffu, Lw, o));
-    const uint32_t steps = (Lw + T - 1 + 3) & ~3u;
+    const uint32_t steps = (Lw + kSkew * (T - 1) + 3) & ~3u;
     const uint32_t blocks_real = L / 4;  // 4-column blocks of this unit (L is a multiple of 4)
 
     V best = vzero;
@@ -281,11 +287,21 @@ __device__ __forceinline__ void process_chunk(const WavefrontArgs& a, const BinA
         V Hl[R], Fr[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) { Hl[r] = vzero; Fr[r] = vzero; }
-        V hb_out = vzero, eb_out = vzero, hdiag0 = vzero;
+        // Thread t works on column s - 2t at step s, so the thread above produced
+        // this thread's inputs (its bottom row H, E and the column's codes) two
+        // steps earlier: the inputs of step s + 1 are shuffled at the start of
+        // step s, and the two steps' dependence chains can overlap.
+        V hb_out = vzero, eb_out = vzero, hdiag0 = vzero;  // this thread's last outputs
         uint32_t code_out = kPair ? kPadPair : kPadCode;
-        const uint2* const bnd_in = bnd0 + (p & 1) * half + T;
-        uint2* const bnd_out = bnd0 + ((p + 1) & 1) * half + T;
+        V h_cur = vzero, e_cur = vzero;                     // inputs of the current step
+        uint32_t code_cur = code_out;
+        const uint2* const bnd_in = bnd0 + (p & 1) * half + kSkew * T;
+        uint2* const bnd_out = bnd0 + ((p + 1) & 1) * half + kSkew * T;
         const bool read_bnd = p > 0;
+        auto code_of = [&](const uint2& w, int k) -> uint32_t {
+            const uint32_t v = (k < 2) ? w.x : w.y;
+            return kPair ? ((v >> (16 * (k & 1))) & 0xffffu) : ((v >> (16 * (k & 1) + 8 * half_sel)) & 0xffu);
+        };
 
         // thread 0's codes (4 columns per 8-byte word) and boundary values, one block ahead
         uint2 wq = make_uint2(kPadWord, kPadWord);
@@ -296,6 +312,11 @@ __device__ __forceinline__ void process_chunk(const WavefrontArgs& a, const BinA
                 bq0 = reinterpret_cast<const uint4*>(bnd_in)[0];
                 bq1 = reinterpret_cast<const uint4*>(bnd_in)[1];
             }
+        }
+        if (t == 0) {  // column 0
+            code_cur = code_of(wq, 0);
+            h_cur = (V)bq0.x;
+            e_cur = (V)bq0.y;
         }
 
         for (uint32_t s0 = 0; s0 < steps; s0 += 4) {
@@ -311,23 +332,26 @@ __device__ __forceinline__ void process_chunk(const WavefrontArgs& a, const BinA
             }
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                // inputs from the thread above: its previous step's bottom row and codes
-                V h_in = (V)__shfl_up_sync(0xffffffffu, (uint32_t)hb_out, 1, T);
-                V e_in = (V)__shfl_up_sync(0xffffffffu, (uint32_t)eb_out, 1, T);
-                uint32_t code = __shfl_up_sync(0xffffffffu, code_out, 1, T);
-                if (t == 0) {
-                    const uint32_t w = (k < 2) ? wq.x : wq.y;
-                    code = kPair ? ((w >> (16 * (k & 1))) & 0xffffu)
-                                 : ((w >> (16 * (k & 1) + 8 * half_sel)) & 0xffu);
-                    const uint4& bq = (k < 2) ? bq0 : bq1;
-                    h_in = (V)((k & 1) ? bq.z : bq.x);
-                    e_in = (V)((k & 1) ? bq.w : bq.y);
+                // inputs of step s + 1: the thread above's outputs of step s - 1
+                V h_nxt = (V)__shfl_up_sync(0xffffffffu, (uint32_t)hb_out, 1, T);
+                V e_nxt = (V)__shfl_up_sync(0xffffffffu, (uint32_t)eb_out, 1, T);
+                uint32_t code_nxt = __shfl_up_sync(0xffffffffu, code_out, 1, T);
+                if (t == 0) {  // column s + 1
+                    if (k < 3) {
+                        code_nxt = code_of(wq, k + 1);
+                        const uint4& bq = (k + 1 < 2) ? bq0 : bq1;
+                        h_nxt = (V)(((k + 1) & 1) ? bq.z : bq.x);
+                        e_nxt = (V)(((k + 1) & 1) ? bq.w : bq.y);
+                    } else {
+                        code_nxt = code_of(wn, 0);
+                        h_nxt = (V)bn0.x;
+                        e_nxt = (V)bn0.y;
+                    }
                 }
-                code_out = code;
                 typename Mode::template Cols<T, R> cs;
-                cs.load(prof, code, t);
+                cs.load(prof, code_cur, t);
                 V diag = hdiag0;
-                V E = e_in;
+                V E = e_cur;
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
                     const V sc = (V)cs.row(r);
@@ -342,9 +366,14 @@ __device__ __forceinline__ void process_chunk(const WavefrontArgs& a, const BinA
                 }
                 hb_out = Hl[R - 1];
                 eb_out = E;
-                hdiag0 = h_in;
-                if (t == T - 1)  // column s - (T-1), at entry T + that >= 1
-                    bnd_out[(int)(s0 + k) - (T - 1)] = make_uint2((uint32_t)hb_out, (uint32_t)eb_out);
+                code_out = code_cur;
+                hdiag0 = h_cur;
+                h_cur = h_nxt;
+                e_cur = e_nxt;
+                code_cur = code_nxt;
+                if (t == T - 1)  // column s - 2 (T-1), at entry 2T + that >= 2
+                    bnd_out[(int)(s0 + k) - kSkew * (T - 1)] =
+                        make_uint2((uint32_t)hb_out, (uint32_t)eb_out);
             }
             wq = wn;
             bq0 = bn0;
@@ -379,6 +408,280 @@ __device__ __forceinline__ void process_chunk(const WavefrontArgs& a, const BinA
     }
 }
 
+// ---------------------------------------------------------------------------
+// Score-profile ring: one query, two database sequences per group
+// ---------------------------------------------------------------------------
+//
+// The packed score of query row i against column j of a pair is
+// (fsbt(q_i, dA_j), fsbt(q_i, dB_j)). ModePairDb merges the two int8 query
+// profile entries with a byte permute for every cell pair. Here each warp
+// keeps instead a ring of packed words (fsbt(c, dA_j), fsbt(c, dB_j)) for
+// every query code c and a window of recent columns j of its pairs: the
+// score profile of Section III.B.2, built on the fly per column rather than
+// for whole sequences. A thread reads the packed score of each of its rows
+// with one shared-memory load; the permutes drop from one per (row, column)
+// to one per (code, column).
+//
+// Ring layout, in 32-bit words per warp: code row c (0..A, row A all zeros
+// for rows past the query) at c * kRingRowWords; slot s of group g at
+// s * G + g (G = 32 / T groups per warp). Column j of a group lives in slot
+// j mod W (W = 2T) and, when j mod W < 8, also in slot W + (j mod W), so a
+// thread addresses the 8 columns of one step block as base + 0..7 without a
+// wrap. The T threads of a group read T consecutive columns at once, which
+// fall in distinct banks (slot mod 8 differs within a group and g separates
+// the groups; for T = 32 slot mod 32 differs), and kRingRowWords is a
+// multiple of 32, so the code of the row does not move the bank.
+struct ModeRing {
+    static constexpr bool kRing = true;
+};
+
+constexpr int kRingRowWords = 96;  // 24 slots x 4 groups (T = 8) or 96 slots x 1 group (T = 32)
+constexpr int kRingBlock = 8;      // steps per block = columns built per block
+constexpr int kStageWords = 18;    // per group: 8 boundary entries of (H, E), padded against conflicts
+constexpr uint32_t kMtBytes = kProfileRows * 32;  // fsbt by database code: [33][32 query codes] int8
+constexpr uint32_t kRingOffset = kMtBytes + kWarps * 4 * kStageWords * 4;
+
+__host__ __device__ constexpr size_t ring_smem_bytes(uint32_t alphabet) {
+    return kRingOffset + (size_t)kWarps * (alphabet + 1) * kRingRowWords * 4;
+}
+
+__device__ __forceinline__ uint32_t lds_u32(uint32_t addr) {
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr));
+    return v;
+}
+__device__ __forceinline__ uint2 lds_u64(uint32_t addr) {
+    uint2 v;
+    asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(addr));
+    return v;
+}
+__device__ __forceinline__ void sts_u32(uint32_t addr, uint32_t v) {
+    asm volatile("st.shared.u32 [%0], %1;" ::"r"(addr), "r"(v));
+}
+__device__ __forceinline__ void sts_u64(uint32_t addr, uint2 v) {
+    asm volatile("st.shared.v2.u32 [%0], {%1, %2};" ::"r"(addr), "r"(v.x), "r"(v.y));
+}
+
+// Once per block: the matrix by database code, and every warp's all-zero row.
+__device__ __forceinline__ void ring_setup(const WavefrontArgs& a, uint8_t* smem) {
+    const uint32_t A = a.alphabet;
+    for (uint32_t idx = threadIdx.x; idx < kProfileRows * 32; idx += kThreads) {
+        const uint32_t d = idx / 32, c = idx % 32;
+        smem[idx] = (uint8_t)((c < A && d < A) ? a.matrix[c * A + d] : 0);
+    }
+    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint32_t* zero_row = reinterpret_cast<uint32_t*>(smem + kRingOffset) +
+                         (size_t)warp * (A + 1) * kRingRowWords + A * kRingRowWords;
+    for (uint32_t w = lane; w < kRingRowWords; w += 32) zero_row[w] = 0;
+    __syncthreads();
+}
+
+// The pair unit of one group against one query, as process_chunk for
+// ModePairDb, with the score-profile ring instead of the int8 query profile.
+template <int T, int R>
+__device__ __forceinline__ void process_chunk_ring(const WavefrontArgs& a, const BinArgs& bin,
+                                                   uint64_t base, uint64_t n_units,
+                                                   const ItemQuery& iq, uint8_t* smem,
+                                                   int32_t thr16) {
+    using Lane = LaneS16x2;
+    using V = uint32_t;
+    constexpr int G = 32 / T;
+    constexpr int TR = T * R;
+    constexpr uint32_t W = 2 * T;
+    constexpr uint32_t kSlot = G * 4;                 // bytes from one slot to the next
+    constexpr uint32_t kCodeBytes = kRingRowWords * 4;
+    constexpr uint32_t kSplit = T / kRingBlock;       // threads sharing one built column
+    constexpr uint32_t kPadPair = kPadCode | (kPadCode << 8);
+    static_assert(W >= T + kRingBlock - 1 && (W & (W - 1)) == 0, "ring window");
+    static_assert((W + kRingBlock) * G <= kRingRowWords && (kRingRowWords % 32) == 0, "ring row");
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane / T, t = lane % T;
+    const uint32_t A = a.alphabet;
+    const uint32_t P = (iq.la + TR - 1) / TR;
+    const uint64_t slot = ((uint64_t)blockIdx.x * kWarps + warp) * G + g;
+    const uint64_t half = bin.bstride / 2;
+    uint2* const bnd0 = bin.boundary + slot * bin.bstride;
+
+    const uint32_t smem_s = (uint32_t)__cvta_generic_to_shared(smem);
+    const uint32_t ring_s = smem_s + kRingOffset + (uint32_t)warp * (A + 1) * kCodeBytes + g * 4;
+    const uint32_t stage_s = smem_s + kMtBytes + (uint32_t)(warp * 4 + g) * kStageWords * 4;
+    const uint4* const mt = reinterpret_cast<const uint4*>(smem);
+
+    const V vbeta = Lane::splat(-a.beta);
+    const V valpha = Lane::splat(-a.alpha);
+    const V vzero = 0;
+
+    // ---- locate this group's unit (a pair of sequences) ----
+    const uint64_t u = base + (uint64_t)warp * G + g;
+    const bool have = u < n_units;
+    uint64_t sp = 0;
+    uint32_t L = 0;
+    const uint8_t* stream = a.tile_data;
+    if (have) {
+        sp = 2 * (bin.first_unit + u);
+        const uint64_t tile = sp / kTileSeqs;
+        const uint32_t pslot = (uint32_t)((sp >> 1) & (kTilePairs - 1));
+        L = a.tile_len[tile];
+        stream = a.tile_data + a.tile_off[tile] + pslot * 8;
+    }
+    uint32_t Lw = L;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) Lw = max(Lw, __shfl_xor_sync(0xffffffffu, Lw, o));
+    const uint32_t steps = (Lw + T - 1 + kRingBlock - 1) & ~(uint32_t)(kRingBlock - 1);
+
+    // what this thread builds: column (block start + bcol), codes bq, bq + kSplit, ...
+    const uint32_t bcol = (uint32_t)t % kRingBlock;
+    const uint32_t bq = (uint32_t)t / kRingBlock;
+    const uint32_t bsel = bq | ((8u | bq) << 4) | ((4u + bq) << 8) | ((12u + bq) << 12);
+
+    V best = vzero;
+    for (uint32_t p = 0; p < P; ++p) {
+        // ring addresses of this thread's rows at the first block (slot of column -t)
+        uint32_t cur[R];
+        const uint32_t blk0 = (W - (uint32_t)t) & (W - 1);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const uint32_t row = p * TR + (uint32_t)t * R + r;
+            uint32_t c = A;
+            if (row < iq.la) {
+                const uint32_t qc = iq.qa[row];
+                c = qc < A ? qc : A;
+            }
+            cur[r] = ring_s + c * kCodeBytes + blk0 * kSlot;
+        }
+        V Hl[R], Fr[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) { Hl[r] = vzero; Fr[r] = vzero; }
+        V hb_out = vzero, eb_out = vzero, hdiag0 = vzero;
+        const uint2* const bnd_in = bnd0 + (p & 1) * half + T;
+        uint2* const bnd_out = bnd0 + ((p + 1) & 1) * half + T;
+        const bool read_bnd = p > 0;
+        // boundary entry of column bcol of the next block (threads below kRingBlock stage it)
+        uint2 bnext = make_uint2(0, 0);
+        if (t < kRingBlock && read_bnd && bcol < L) bnext = bnd_in[bcol];
+
+        for (uint32_t s0 = 0; s0 < steps; s0 += kRingBlock) {
+            __syncwarp();  // the slots rewritten below are no longer read
+            {
+                const uint32_t j = s0 + bcol;
+                uint32_t pc = kPadPair;
+                if (j < L) pc = *reinterpret_cast<const uint16_t*>(stream + (size_t)(j >> 2) * 32 + (j & 3) * 2);
+                const uint4 a0 = mt[(pc & 0xffu) * 2], a1 = mt[(pc & 0xffu) * 2 + 1];
+                const uint4 b0 = mt[(pc >> 8) * 2], b1 = mt[(pc >> 8) * 2 + 1];
+                const uint32_t wa[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+                const uint32_t wb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+                const uint32_t js = j & (W - 1);
+                const uint32_t at = ring_s + js * kSlot;
+                const bool dup = js < kRingBlock;
+                if constexpr (kSplit == 1) {
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        if (4u * k >= A) break;
+#pragma unroll
+                        for (int b = 0; b < 4; ++b) {
+                            const uint32_t c = 4u * k + b;
+                            if (c < A) {
+                                const uint32_t v = prmt(wa[k], wb[k], b | ((8u | b) << 4) |
+                                                                          ((4u + b) << 8) | ((12u + b) << 12));
+                                sts_u32(at + c * kCodeBytes, v);
+                                if (dup) sts_u32(at + c * kCodeBytes + W * kSlot, v);
+                            }
+                        }
+                    }
+                } else {
+                    static_assert(kSplit == 4, "codes per word");
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        if (4u * k >= A) break;
+                        const uint32_t c = 4u * k + bq;
+                        if (c < A) {
+                            const uint32_t v = prmt(wa[k], wb[k], bsel);
+                            sts_u32(at + c * kCodeBytes, v);
+                            if (dup) sts_u32(at + c * kCodeBytes + W * kSlot, v);
+                        }
+                    }
+                }
+            }
+            if (s0 == 0 && t + 1 < T) {
+                // columns -(T-1) .. -1 (slots W-T+1 .. W-1) score 0 at the start of a pass
+                const uint32_t at = ring_s + (W - T + 1 + (uint32_t)t) * kSlot;
+                for (uint32_t c = 0; c < A; ++c) sts_u32(at + c * kCodeBytes, 0u);
+            }
+            if (t < kRingBlock) sts_u64(stage_s + (uint32_t)t * 8, bnext);
+            __syncwarp();  // this block's columns and boundary entries are visible
+            if (t < kRingBlock) {
+                const uint32_t jn = s0 + kRingBlock + (uint32_t)t;
+                bnext = (read_bnd && jn < L) ? bnd_in[jn] : make_uint2(0, 0);
+            }
+#pragma unroll
+            for (int k = 0; k < kRingBlock; ++k) {
+                V h_in = (V)__shfl_up_sync(0xffffffffu, (uint32_t)hb_out, 1, T);
+                V e_in = (V)__shfl_up_sync(0xffffffffu, (uint32_t)eb_out, 1, T);
+                if (t == 0) {
+                    const uint2 bv = lds_u64(stage_s + k * 8);
+                    h_in = bv.x;
+                    e_in = bv.y;
+                }
+                V diag = hdiag0;
+                V E = e_in;
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const V sc = lds_u32(cur[r] + k * kSlot);
+                    const V x = Lane::vadd(diag, sc);              // H[i-1][j-1] + fsbt
+                    const V H = Lane::max3_relu(x, E, Fr[r]);      // H[i][j]
+                    diag = Hl[r];
+                    Hl[r] = H;
+                    const V hb = Lane::vadd(H, vbeta);             // H[i][j] - beta
+                    E = Lane::addmax(E, valpha, hb);               // E[i+1][j]
+                    Fr[r] = Lane::addmax(Fr[r], valpha, hb);       // F[i][j+1]
+                    best = Lane::vmax(best, x);                    // max H = max(0, max x)
+                }
+                hb_out = Hl[R - 1];
+                eb_out = E;
+                hdiag0 = h_in;
+                if (t == T - 1)
+                    bnd_out[(int)(s0 + k) - (T - 1)] = make_uint2((uint32_t)hb_out, (uint32_t)eb_out);
+            }
+            // next block: slots advance by 8, wrapping at W
+            const uint32_t blk = (s0 - (uint32_t)t) & (W - 1);
+            const uint32_t delta = (blk + kRingBlock < W ? kRingBlock : kRingBlock - W) * kSlot;
+#pragma unroll
+            for (int r = 0; r < R; ++r) cur[r] += delta;
+        }
+    }
+
+    // ---- group maximum and results ----
+#pragma unroll
+    for (int o = T / 2; o > 0; o >>= 1)
+        best = Lane::vmax(best, (V)__shfl_xor_sync(0xffffffffu, (uint32_t)best, o, T));
+    if (!have || t != 0) return;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int32_t v = (int16_t)(h ? ((uint32_t)best >> 16) : ((uint32_t)best & 0xffffu));
+        const uint64_t seq = sp + h;
+        const uint32_t id = a.sorted_ids[seq];
+        if (id == 0xffffffffu) continue;
+        if (v >= thr16) {  // rescored in int32; -1 marks it until then
+            const uint32_t k = atomicAdd(a.flag_count, 1u);
+            if (k < a.flag_cap) a.flag_list[k] = make_uint2(iq.ia, (uint32_t)seq);
+            a.scores[(uint64_t)iq.ia * a.score_stride + id] = -1;
+        } else {
+            a.scores[(uint64_t)iq.ia * a.score_stride + id] = v;
+        }
+    }
+}
+
+template <class Mode, int T, int R>
+__device__ __forceinline__ void run_chunk(const WavefrontArgs& a, const BinArgs& bin, uint64_t base,
+                                          uint64_t n_units, const ItemQuery& iq, uint8_t* smem,
+                                          int32_t thr16) {
+    if constexpr (Mode::kRing)
+        process_chunk_ring<T, R>(a, bin, base, n_units, iq, smem, thr16);
+    else
+        process_chunk<Mode, T, R>(a, bin, base, n_units, iq, smem, thr16);
+}
+
 __device__ __forceinline__ ItemQuery item_query(const WavefrontArgs& a, uint32_t k) {
     ItemQuery iq;
     if (a.pairs) {
@@ -405,7 +708,7 @@ __device__ __forceinline__ ItemQuery item_query(const WavefrontArgs& a, uint32_t
 // longest work starts first and one database chunk is reused across the
 // query items from L2.
 template <class Mode, int TS, int RS, int TL, int RL>
-__global__ void __launch_bounds__(kThreads) search_kernel(const WavefrontArgs a) {
+__global__ void __launch_bounds__(kThreads, 2) search_kernel(const WavefrontArgs a) {
     extern __shared__ __align__(16) uint8_t prof[];
     __shared__ uint32_t s_item;
     constexpr uint32_t UNITS_L = kWarps * (32 / TL);
@@ -421,6 +724,7 @@ __global__ void __launch_bounds__(kThreads) search_kernel(const WavefrontArgs a)
     atomicMax(&s_smax, mx);
     __syncthreads();
     const int32_t thr16 = 32767 - s_smax;
+    if constexpr (Mode::kRing) ring_setup(a, prof);
 
     if (a.item_prefix) {
         // serving wave: each pair scans its own range of bin-1 chunks
@@ -436,7 +740,7 @@ __global__ void __launch_bounds__(kThreads) search_kernel(const WavefrontArgs a)
                 if (a.item_prefix[mid] <= it) lo = mid; else hi = mid;
             }
             const uint64_t chunk = (uint64_t)a.pair_chunk0[lo] + (it - a.item_prefix[lo]);
-            process_chunk<Mode, TS, RS>(a, a.bin[1], chunk * UNITS_S, a.bin[1].n_units,
+            run_chunk<Mode, TS, RS>(a, a.bin[1], chunk * UNITS_S, a.bin[1].n_units,
                                         item_query(a, lo), prof, thr16);
             __syncthreads();
         }
@@ -454,12 +758,12 @@ __global__ void __launch_bounds__(kThreads) search_kernel(const WavefrontArgs a)
         if (it >= items) break;
         if (it < items_long) {
             const ItemQuery iq = item_query(a, (uint32_t)(it % n_items_q));
-            process_chunk<Mode, TL, RL>(a, a.bin[0], (it / n_items_q) * UNITS_L, a.bin[0].n_units,
+            run_chunk<Mode, TL, RL>(a, a.bin[0], (it / n_items_q) * UNITS_L, a.bin[0].n_units,
                                         iq, prof, thr16);
         } else {
             const uint64_t is = it - items_long;
             const ItemQuery iq = item_query(a, (uint32_t)(is % n_items_q));
-            process_chunk<Mode, TS, RS>(a, a.bin[1], (is / n_items_q) * UNITS_S, a.bin[1].n_units,
+            run_chunk<Mode, TS, RS>(a, a.bin[1], (is / n_items_q) * UNITS_S, a.bin[1].n_units,
                                         iq, prof, thr16);
         }
         __syncthreads();  // s_item is rewritten by the next iteration
@@ -491,8 +795,16 @@ const Entry kEntries[] = {
     SWGB_ENTRY(1, ModeQueryPair, 12), SWGB_ENTRY(1, ModeQueryPair, 16),
     SWGB_ENTRY(1, ModeQueryPair, 20), SWGB_ENTRY(1, ModeQueryPair, 24),
     SWGB_ENTRY(2, ModeInt32, 16),
+#define SWGB_RING(R) {3, R, search_kernel<ModeRing, kShortT, R, kLongT, kLongR>, 0}
+    SWGB_RING(8), SWGB_RING(12), SWGB_RING(16), SWGB_RING(20), SWGB_RING(24),
+#undef SWGB_RING
 };
 #undef SWGB_ENTRY
+
+// Dynamic shared memory of one launch (the ring grows with the alphabet).
+size_t entry_smem(const Entry& e, uint32_t alphabet) {
+    return e.mode == 3 ? ring_smem_bytes(alphabet) : e.smem;
+}
 
 const Entry* find_entry(const KernelChoice& kc) {
     for (const Entry& e : kEntries)
@@ -510,12 +822,13 @@ int wavefront_occupancy(const KernelChoice& kc, int* threads_per_block) {
     const Entry* e = find_entry(kc);
     if (threads_per_block) *threads_per_block = kThreads;
     if (!e) return 0;
-    if (e->smem > 48 * 1024 &&
-        cudaFuncSetAttribute(e->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)e->smem) !=
+    const size_t smem = entry_smem(*e, 32);  // the largest alphabet
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(e->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess)
         return 0;
     int blocks = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, e->fn, kThreads, e->smem) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, e->fn, kThreads, smem) !=
         cudaSuccess)
         return 0;
     return blocks;
@@ -526,12 +839,14 @@ cudaError_t launch_wavefront(const KernelChoice& kc, const WavefrontArgs& a, int
     const Entry* e = find_entry(kc);
     if (!e) return cudaErrorInvalidValue;
     if (grid <= 0) return cudaErrorInvalidConfiguration;
-    if (e->smem > 48 * 1024) {
-        cudaError_t err =
-            cudaFuncSetAttribute(e->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)e->smem);
+    if (a.alphabet < 1 || a.alphabet > 32) return cudaErrorInvalidValue;
+    const size_t smem = entry_smem(*e, a.alphabet);
+    if (smem > 48 * 1024) {
+        cudaError_t err = cudaFuncSetAttribute(e->fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)entry_smem(*e, 32));
         if (err != cudaSuccess) return err;
     }
-    e->fn<<<grid, kThreads, e->smem, stream>>>(a);
+    e->fn<<<grid, kThreads, smem, stream>>>(a);
     return cudaGetLastError();
 }
 

@@ -25,6 +25,16 @@ def _db_from_lengths(lengths, seed, A=20):
     return res, off
 
 
+# single queries run in the score-profile ring kernel by default; the flag selects the
+# int8 query-profile kernel, so every test below runs both
+KERNELS = {"ring": 0, "qprof": sw.SW_DB_FLAG_QUERY_PROFILE}
+
+
+@pytest.fixture(params=sorted(KERNELS))
+def kflags(request):
+    return KERNELS[request.param]
+
+
 def _check(db, res, off, q, M, alpha, beta, k, *, expect_recompute=None):
     scores, ts, ti, stats = sw.sw_search(db, q, M, alpha, beta, k)
     es = oracle.scores(q, res, off, M, alpha, beta)
@@ -38,40 +48,40 @@ def _check(db, res, off, q, M, alpha, beta, k, *, expect_recompute=None):
     return scores, stats
 
 
-def test_config0_full():
+def test_config0_full(kflags):
     w = synth.config0()
-    with sw.sw_db_load(w.residues, w.offsets) as db:
+    with sw.sw_db_load(w.residues, w.offsets, flags=kflags) as db:
         _check(db, w.residues, w.offsets, w.queries[0], w.matrix, w.alpha, w.beta, w.top_k,
                expect_recompute=False)
 
 
 @pytest.mark.parametrize("qlen", [1, 2, 7, 63, 64, 65, 96, 127, 128, 129, 160, 161, 192, 300, 513, 1100])
-def test_query_lengths_across_pass_boundaries(qlen):
+def test_query_lengths_across_pass_boundaries(qlen, kflags):
     lengths = synth.gen_lengths(1500, synth.db_qtable(), 31, 1)
     res, off = _db_from_lengths(lengths, 31)
     q = synth.make_queries([qlen], 1000 + qlen)[0]
-    with sw.sw_db_load(res, off) as db:
+    with sw.sw_db_load(res, off, flags=kflags) as db:
         _check(db, res, off, q, synth.BLOSUM62, 1, 11, 10)
 
 
-def test_ragged_database_edges():
+def test_ragged_database_edges(kflags):
     # empty sequences, lengths around the 4-column blocks and tile boundaries,
     # a count that is not a multiple of 8, and a few long sequences
     lens = [0, 1, 2, 3, 4, 5, 7, 8, 9, 15, 16, 17, 31, 32, 33, 0, 0, 100, 3000, 3001, 3004, 4100, 6, 1]
     res, off = _db_from_lengths(lens, 5)
     for qlen in (1, 50, 200):
         q = synth.make_queries([qlen], 77 + qlen)[0]
-        with sw.sw_db_load(res, off) as db:
+        with sw.sw_db_load(res, off, flags=kflags) as db:
             _check(db, res, off, q, synth.BLOSUM62, 1, 11, 30)
 
 
 @pytest.mark.parametrize("threshold", [16, 64, 300])
-def test_long_sequence_kernel(threshold):
+def test_long_sequence_kernel(threshold, kflags):
     """Sequences above the threshold go to the warp-per-pair kernel (T = 32)."""
     lengths = synth.gen_lengths(700, synth.db_qtable(), 41, 1)
     res, off = _db_from_lengths(lengths, 41)
     q = synth.make_queries([700], 4242)[0]
-    with sw.sw_db_load(res, off, long_threshold=threshold) as db:
+    with sw.sw_db_load(res, off, long_threshold=threshold, flags=kflags) as db:
         info = db.info()
         assert info["n_long"] == int((lengths > threshold).sum())
         _check(db, res, off, q, synth.BLOSUM62, 1, 11, 10)
@@ -79,17 +89,17 @@ def test_long_sequence_kernel(threshold):
 
 @pytest.mark.parametrize("A", [4, 20, 24, 32])
 @pytest.mark.parametrize("ab", [(1, 11), (0, 5), (5, 2), (0, 0), (3, 0), (2, 12)])
-def test_alphabets_and_penalties(A, ab):
+def test_alphabets_and_penalties(A, ab, kflags):
     rng = np.random.default_rng(A * 100 + ab[0] * 10 + ab[1])
     M = rng.integers(-6, 9, size=(A, A)).astype(np.int8)  # asymmetric
     lengths = synth.gen_lengths(400, synth.db_qtable(), 51, 1) // 3 + 1
     res, off = _db_from_lengths(lengths, 51, A)
     q = rng.integers(0, A, size=150).astype(np.uint8)
-    with sw.sw_db_load(res, off, alphabet=A) as db:
+    with sw.sw_db_load(res, off, alphabet=A, flags=kflags) as db:
         _check(db, res, off, q, M, ab[0], ab[1], 15)
 
 
-def test_int16_saturation_is_rescored_exactly():
+def test_int16_saturation_is_rescored_exactly(kflags):
     """Self-similar pairs under a scaled matrix exceed the 16-bit range and are rescored."""
     q = synth.make_queries([900], 9)[0]
     lengths = synth.gen_lengths(300, synth.db_qtable(), 61, 1)
@@ -102,7 +112,7 @@ def test_int16_saturation_is_rescored_exactly():
     off = np.zeros(len(seqs) + 1, np.uint64)
     off[1:] = np.cumsum([s.size for s in seqs])
     M = (synth.BLOSUM62.astype(np.int32) * 8).astype(np.int8)
-    with sw.sw_db_load(res, off) as db:
+    with sw.sw_db_load(res, off, flags=kflags) as db:
         scores, stats = _check(db, res, off, q, M, 8, 88, 10, expect_recompute=True)
     assert scores.max() > 32767
 

@@ -21,7 +21,7 @@ def test_autotune_cache_and_exact_results(tmp_path):
     with sw.sw_db_load(res, off) as db:
         t1 = sw.sw_db_autotune(db, synth.BLOSUM62, 1, 11, cache)
         assert not t1["from_cache"]
-        for mode in ("pair_db", "query_pair"):
+        for mode in ("pair_db", "query_pair", "pair_ring"):
             row = t1["ns_per_row_residue"][mode]
             assert all(v > 0 for v in row), (mode, row)
         assert t1["ns_per_row_residue"]["int32"][2] > 0  # int32 runs with 16 rows per lane only
@@ -29,8 +29,9 @@ def test_autotune_cache_and_exact_results(tmp_path):
         assert os.path.exists(cache) and "query_pair" in json.load(open(cache))
         t2 = sw.sw_db_autotune(db, synth.BLOSUM62, 1, 11, cache)
         assert t2["from_cache"]
-        assert np.allclose(t2["ns_per_row_residue"]["pair_db"], t1["ns_per_row_residue"]["pair_db"],
-                           rtol=1e-4)
+        for mode in ("pair_db", "pair_ring"):
+            assert np.allclose(t2["ns_per_row_residue"][mode], t1["ns_per_row_residue"][mode],
+                               rtol=1e-4)
         # tuned searches are still exact
         qs = synth.make_queries([150, 700, 33], 402)
         for q in qs:
