@@ -38,6 +38,7 @@
 //    at most thr16 - beta), which is computed exactly, so the running maximum
 //    of a lane that ever exceeded thr16 ends above it.
 #include <cuda_runtime.h>
+#include <algorithm>
 #include <cstdint>
 #include <type_traits>
 
@@ -422,27 +423,54 @@ __device__ __forceinline__ void process_chunk(const WavefrontArgs& a, const BinA
 // with one shared-memory load; the permutes drop from one per (row, column)
 // to one per (code, column).
 //
+// Thread t of a group works on column s - S t at step s. With S = 2 its
+// inputs (the thread above's bottom row) are ready two steps ahead and are
+// shuffled one step early, so consecutive steps' dependence chains overlap.
+//
 // Ring layout, in 32-bit words per warp: code row c (0..A, row A all zeros
-// for rows past the query) at c * kRingRowWords; slot s of group g at
-// s * G + g (G = 32 / T groups per warp). Column j of a group lives in slot
-// j mod W (W = 2T) and, when j mod W < 8, also in slot W + (j mod W), so a
-// thread addresses the 8 columns of one step block as base + 0..7 without a
-// wrap. The T threads of a group read T consecutive columns at once, which
-// fall in distinct banks (slot mod 8 differs within a group and g separates
-// the groups; for T = 32 slot mod 32 differs), and kRingRowWords is a
-// multiple of 32, so the code of the row does not move the bank.
+// for rows past the query) at c * RingGeom::kRowWords. S = 1: column j of
+// group g in slot j mod W at word slot * G + g (G = 32 / T groups per warp).
+// S = 2: the even and odd columns in two planes, column j in plane j & 1 at
+// slot (j >> 1) mod W. A slot below D is also stored at W + slot, so a
+// thread addresses the columns of one 8-step block from one base without a
+// wrap. The T threads of a group read T columns of one parity (S = 2) or T
+// consecutive columns (S = 1) at once; their slots differ mod 8 (T = 8: with
+// g in the low bits the warp hits 32 distinct banks) or mod 32 (T = 32), and
+// kRowWords is a multiple of 32, so the code of a row does not move its bank.
+template <int S>
 struct ModeRing {
     static constexpr bool kRing = true;
+    static constexpr int kSkew = S;
 };
 
-constexpr int kRingRowWords = 96;  // 24 slots x 4 groups (T = 8) or 96 slots x 1 group (T = 32)
 constexpr int kRingBlock = 8;      // steps per block = columns built per block
 constexpr int kStageWords = 18;    // per group: 8 boundary entries of (H, E), padded against conflicts
 constexpr uint32_t kMtBytes = kProfileRows * 32;  // fsbt by database code: [33][32 query codes] int8
 constexpr uint32_t kRingOffset = kMtBytes + kWarps * 4 * kStageWords * 4;
+// The two-column skew needs a larger window; it keeps two blocks per SM up to this alphabet.
+constexpr uint32_t kRing2MaxAlphabet = 20;
 
-__host__ __device__ constexpr size_t ring_smem_bytes(uint32_t alphabet) {
-    return kRingOffset + (size_t)kWarps * (alphabet + 1) * kRingRowWords * 4;
+template <int S>
+__host__ __device__ constexpr int ring_row_words() { return S == 1 ? 96 : 160; }
+
+template <int T, int S>
+struct RingGeom {
+    static constexpr int G = 32 / T;
+    static constexpr uint32_t W = S == 1 ? 2 * T : (T == 8 ? 16 : 64);  // slots in the window
+    static constexpr uint32_t D = kRingBlock / S;                        // slots stored twice
+    static constexpr uint32_t kSlot = G * 4;                             // bytes between slots
+    static constexpr uint32_t kPlane = (W + D) * G * 4;                  // bytes between planes
+    static constexpr uint32_t kCodeBytes = ring_row_words<S>() * 4;
+    static_assert(S * (W + D) * G <= (uint32_t)ring_row_words<S>() && ring_row_words<S>() % 32 == 0,
+                  "ring row");
+    // live window: the 8 columns built at a block start must not overwrite a column
+    // still read in that block (the oldest is S (T - 1) columns behind)
+    static_assert(S == 1 ? W >= T + kRingBlock - 1 : W >= T + 3, "ring window");
+    static_assert((W % (T == 8 ? 8 : 32)) == 0, "bank pattern");
+};
+
+__host__ __device__ constexpr size_t ring_smem_bytes(uint32_t alphabet, int S) {
+    return kRingOffset + (size_t)kWarps * (alphabet + 1) * (S == 1 ? ring_row_words<1>() : ring_row_words<2>()) * 4;
 }
 
 __device__ __forceinline__ uint32_t lds_u32(uint32_t addr) {
@@ -450,10 +478,18 @@ __device__ __forceinline__ uint32_t lds_u32(uint32_t addr) {
     asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr));
     return v;
 }
-__device__ __forceinline__ uint2 lds_u64(uint32_t addr) {
-    uint2 v;
-    asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(addr));
-    return v;
+// The value of the thread above (shfl.up within segments of T threads); the
+// first thread of a segment, which has none, loads it from shared memory.
+template <int T>
+__device__ __forceinline__ uint32_t shfl_up_or_lds(uint32_t v, uint32_t addr) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "shfl.sync.up.b32 %0|p, %1, 1, %3, -1;\n\t"
+        "@!p ld.shared.u32 %0, [%2];\n\t}"
+        : "=r"(r)
+        : "r"(v), "r"(addr), "n"((32 - T) << 8));
+    return r;
 }
 __device__ __forceinline__ void sts_u32(uint32_t addr, uint32_t v) {
     asm volatile("st.shared.u32 [%0], %1;" ::"r"(addr), "r"(v));
@@ -463,6 +499,7 @@ __device__ __forceinline__ void sts_u64(uint32_t addr, uint2 v) {
 }
 
 // Once per block: the matrix by database code, and every warp's all-zero row.
+template <int S>
 __device__ __forceinline__ void ring_setup(const WavefrontArgs& a, uint8_t* smem) {
     const uint32_t A = a.alphabet;
     for (uint32_t idx = threadIdx.x; idx < kProfileRows * 32; idx += kThreads) {
@@ -470,30 +507,31 @@ __device__ __forceinline__ void ring_setup(const WavefrontArgs& a, uint8_t* smem
         smem[idx] = (uint8_t)((c < A && d < A) ? a.matrix[c * A + d] : 0);
     }
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    constexpr uint32_t kRow = ring_row_words<S>();
     uint32_t* zero_row = reinterpret_cast<uint32_t*>(smem + kRingOffset) +
-                         (size_t)warp * (A + 1) * kRingRowWords + A * kRingRowWords;
-    for (uint32_t w = lane; w < kRingRowWords; w += 32) zero_row[w] = 0;
+                         (size_t)warp * (A + 1) * kRow + A * kRow;
+    for (uint32_t w = lane; w < kRow; w += 32) zero_row[w] = 0;
     __syncthreads();
 }
 
 // The pair unit of one group against one query, as process_chunk for
 // ModePairDb, with the score-profile ring instead of the int8 query profile.
-template <int T, int R>
+template <int T, int R, int S>
 __device__ __forceinline__ void process_chunk_ring(const WavefrontArgs& a, const BinArgs& bin,
                                                    uint64_t base, uint64_t n_units,
                                                    const ItemQuery& iq, uint8_t* smem,
                                                    int32_t thr16) {
     using Lane = LaneS16x2;
     using V = uint32_t;
-    constexpr int G = 32 / T;
+    using Geo = RingGeom<T, S>;
+    constexpr int G = Geo::G;
     constexpr int TR = T * R;
-    constexpr uint32_t W = 2 * T;
-    constexpr uint32_t kSlot = G * 4;                 // bytes from one slot to the next
-    constexpr uint32_t kCodeBytes = kRingRowWords * 4;
+    constexpr uint32_t W = Geo::W;
+    constexpr uint32_t kSlot = Geo::kSlot;
+    constexpr uint32_t kCodeBytes = Geo::kCodeBytes;
     constexpr uint32_t kSplit = T / kRingBlock;       // threads sharing one built column
     constexpr uint32_t kPadPair = kPadCode | (kPadCode << 8);
-    static_assert(W >= T + kRingBlock - 1 && (W & (W - 1)) == 0, "ring window");
-    static_assert((W + kRingBlock) * G <= kRingRowWords && (kRingRowWords % 32) == 0, "ring row");
+    constexpr uint32_t kAdvance = kRingBlock / S;     // slots per block
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = lane / T, t = lane % T;
@@ -528,16 +566,28 @@ __device__ __forceinline__ void process_chunk_ring(const WavefrontArgs& a, const
     uint32_t Lw = L;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) Lw = max(Lw, __shfl_xor_sync(0xffffffffu, Lw, o));
-    const uint32_t steps = (Lw + T - 1 + kRingBlock - 1) & ~(uint32_t)(kRingBlock - 1);
+    const uint32_t steps = (Lw + S * (T - 1) + kRingBlock - 1) & ~(uint32_t)(kRingBlock - 1);
 
     // what this thread builds: column (block start + bcol), codes bq, bq + kSplit, ...
     const uint32_t bcol = (uint32_t)t % kRingBlock;
     const uint32_t bq = (uint32_t)t / kRingBlock;
     const uint32_t bsel = bq | ((8u | bq) << 4) | ((4u + bq) << 8) | ((12u + bq) << 12);
+    // ring byte offset of column j (code 0; the duplicate is + W * kSlot)
+    auto col_off = [&](uint32_t j, bool& dup) -> uint32_t {
+        if constexpr (S == 1) {
+            const uint32_t js = j & (W - 1);
+            dup = js < Geo::D;
+            return js * kSlot;
+        } else {
+            const uint32_t js = (j >> 1) & (W - 1);
+            dup = js < Geo::D;
+            return (j & 1) * Geo::kPlane + js * kSlot;
+        }
+    };
 
     V best = vzero;
     for (uint32_t p = 0; p < P; ++p) {
-        // ring addresses of this thread's rows at the first block (slot of column -t)
+        // ring addresses of this thread's rows at the first block (slot of column -S t)
         uint32_t cur[R];
         const uint32_t blk0 = (W - (uint32_t)t) & (W - 1);
 #pragma unroll
@@ -553,13 +603,20 @@ __device__ __forceinline__ void process_chunk_ring(const WavefrontArgs& a, const
         V Hl[R], Fr[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) { Hl[r] = vzero; Fr[r] = vzero; }
-        V hb_out = vzero, eb_out = vzero, hdiag0 = vzero;
-        const uint2* const bnd_in = bnd0 + (p & 1) * half + T;
-        uint2* const bnd_out = bnd0 + ((p + 1) & 1) * half + T;
+        V hb_out = vzero, eb_out = vzero, hdiag0 = vzero;  // this thread's last outputs
+        V h_cur = vzero, e_cur = vzero;                     // inputs of the current step (S = 2)
+        const uint2* const bnd_in = bnd0 + (p & 1) * half + S * T;
+        uint2* const bnd_out = bnd0 + ((p + 1) & 1) * half + S * T;
         const bool read_bnd = p > 0;
         // boundary entry of column bcol of the next block (threads below kRingBlock stage it)
         uint2 bnext = make_uint2(0, 0);
         if (t < kRingBlock && read_bnd && bcol < L) bnext = bnd_in[bcol];
+        if constexpr (S == 2) {
+            if (t == 0) {  // column 0
+                h_cur = bnext.x;
+                e_cur = bnext.y;
+            }
+        }
 
         for (uint32_t s0 = 0; s0 < steps; s0 += kRingBlock) {
             __syncwarp();  // the slots rewritten below are no longer read
@@ -571,17 +628,17 @@ __device__ __forceinline__ void process_chunk_ring(const WavefrontArgs& a, const
                 const uint4 b0 = mt[(pc >> 8) * 2], b1 = mt[(pc >> 8) * 2 + 1];
                 const uint32_t wa[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
                 const uint32_t wb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-                const uint32_t js = j & (W - 1);
-                const uint32_t at = ring_s + js * kSlot;
-                const bool dup = js < kRingBlock;
+                bool dup;
+                const uint32_t at = ring_s + col_off(j, dup);
                 if constexpr (kSplit == 1) {
 #pragma unroll
                     for (int k = 0; k < 8; ++k) {
                         if (4u * k >= A) break;
+                        const bool whole = 4u * k + 4 <= A;  // uniform: no per-code test
 #pragma unroll
                         for (int b = 0; b < 4; ++b) {
                             const uint32_t c = 4u * k + b;
-                            if (c < A) {
+                            if (whole || c < A) {
                                 const uint32_t v = prmt(wa[k], wb[k], b | ((8u | b) << 4) |
                                                                           ((4u + b) << 8) | ((12u + b) << 12));
                                 sts_u32(at + c * kCodeBytes, v);
@@ -604,9 +661,13 @@ __device__ __forceinline__ void process_chunk_ring(const WavefrontArgs& a, const
                 }
             }
             if (s0 == 0 && t + 1 < T) {
-                // columns -(T-1) .. -1 (slots W-T+1 .. W-1) score 0 at the start of a pass
+                // columns -S(T-1) .. -1 score 0 at the start of a pass: slots W-T+1 .. W-1
+                // (both planes for S = 2)
                 const uint32_t at = ring_s + (W - T + 1 + (uint32_t)t) * kSlot;
-                for (uint32_t c = 0; c < A; ++c) sts_u32(at + c * kCodeBytes, 0u);
+                for (uint32_t c = 0; c < A; ++c) {
+                    sts_u32(at + c * kCodeBytes, 0u);
+                    if constexpr (S == 2) sts_u32(at + c * kCodeBytes + Geo::kPlane, 0u);
+                }
             }
             if (t < kRingBlock) sts_u64(stage_s + (uint32_t)t * 8, bnext);
             __syncwarp();  // this block's columns and boundary entries are visible
@@ -614,20 +675,38 @@ __device__ __forceinline__ void process_chunk_ring(const WavefrontArgs& a, const
                 const uint32_t jn = s0 + kRingBlock + (uint32_t)t;
                 bnext = (read_bnd && jn < L) ? bnd_in[jn] : make_uint2(0, 0);
             }
+            uint2* const bo = bnd_out + (int)s0 - S * (T - 1);
 #pragma unroll
             for (int k = 0; k < kRingBlock; ++k) {
-                V h_in = (V)__shfl_up_sync(0xffffffffu, (uint32_t)hb_out, 1, T);
-                V e_in = (V)__shfl_up_sync(0xffffffffu, (uint32_t)eb_out, 1, T);
-                if (t == 0) {
-                    const uint2 bv = lds_u64(stage_s + k * 8);
-                    h_in = bv.x;
-                    e_in = bv.y;
+                V h_in, e_in;
+                if constexpr (S == 1) {
+                    h_in = shfl_up_or_lds<T>(hb_out, stage_s + k * 8);
+                    e_in = shfl_up_or_lds<T>(eb_out, stage_s + k * 8 + 4);
+                } else {
+                    // inputs of step s + 1: the thread above's outputs of step s - 1
+                    V h_nxt, e_nxt;
+                    if (k + 1 < kRingBlock) {
+                        h_nxt = shfl_up_or_lds<T>(hb_out, stage_s + (k + 1) * 8);
+                        e_nxt = shfl_up_or_lds<T>(eb_out, stage_s + (k + 1) * 8 + 4);
+                    } else {  // column s + 1 opens the next block: thread 0 holds it
+                        h_nxt = (V)__shfl_up_sync(0xffffffffu, (uint32_t)hb_out, 1, T);
+                        e_nxt = (V)__shfl_up_sync(0xffffffffu, (uint32_t)eb_out, 1, T);
+                        if (t == 0) {
+                            h_nxt = bnext.x;
+                            e_nxt = bnext.y;
+                        }
+                    }
+                    h_in = h_cur;
+                    e_in = e_cur;
+                    h_cur = h_nxt;
+                    e_cur = e_nxt;
                 }
+                const uint32_t koff = S == 1 ? k * kSlot : (k & 1) * Geo::kPlane + (k >> 1) * kSlot;
                 V diag = hdiag0;
                 V E = e_in;
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
-                    const V sc = lds_u32(cur[r] + k * kSlot);
+                    const V sc = lds_u32(cur[r] + koff);
                     const V x = Lane::vadd(diag, sc);              // H[i-1][j-1] + fsbt
                     const V H = Lane::max3_relu(x, E, Fr[r]);      // H[i][j]
                     diag = Hl[r];
@@ -640,12 +719,11 @@ __device__ __forceinline__ void process_chunk_ring(const WavefrontArgs& a, const
                 hb_out = Hl[R - 1];
                 eb_out = E;
                 hdiag0 = h_in;
-                if (t == T - 1)
-                    bnd_out[(int)(s0 + k) - (T - 1)] = make_uint2((uint32_t)hb_out, (uint32_t)eb_out);
+                if (t == T - 1) bo[k] = make_uint2((uint32_t)hb_out, (uint32_t)eb_out);
             }
-            // next block: slots advance by 8, wrapping at W
-            const uint32_t blk = (s0 - (uint32_t)t) & (W - 1);
-            const uint32_t delta = (blk + kRingBlock < W ? kRingBlock : kRingBlock - W) * kSlot;
+            // next block: slots advance by kAdvance, wrapping at W
+            const uint32_t blk = ((s0 / S) - (uint32_t)t) & (W - 1);
+            const uint32_t delta = (blk + kAdvance < W ? kAdvance : kAdvance - W) * kSlot;
 #pragma unroll
             for (int r = 0; r < R; ++r) cur[r] += delta;
         }
@@ -677,7 +755,7 @@ __device__ __forceinline__ void run_chunk(const WavefrontArgs& a, const BinArgs&
                                           uint64_t n_units, const ItemQuery& iq, uint8_t* smem,
                                           int32_t thr16) {
     if constexpr (Mode::kRing)
-        process_chunk_ring<T, R>(a, bin, base, n_units, iq, smem, thr16);
+        process_chunk_ring<T, R, Mode::kSkew>(a, bin, base, n_units, iq, smem, thr16);
     else
         process_chunk<Mode, T, R>(a, bin, base, n_units, iq, smem, thr16);
 }
@@ -724,7 +802,7 @@ __global__ void __launch_bounds__(kThreads, 2) search_kernel(const WavefrontArgs
     atomicMax(&s_smax, mx);
     __syncthreads();
     const int32_t thr16 = 32767 - s_smax;
-    if constexpr (Mode::kRing) ring_setup(a, prof);
+    if constexpr (Mode::kRing) ring_setup<Mode::kSkew>(a, prof);
 
     if (a.item_prefix) {
         // serving wave: each pair scans its own range of bin-1 chunks
@@ -777,6 +855,7 @@ struct Entry {
     int R;
     KernelFn fn;
     size_t smem;
+    int skew;  // ring entries: threads' column skew (1 or 2); 0 otherwise
 };
 
 template <class Mode, int R>
@@ -787,7 +866,7 @@ constexpr size_t smem_of() {
 }
 
 #define SWGB_ENTRY(M, MODE, R) \
-    {M, R, search_kernel<MODE, kShortT, R, kLongT, kLongR>, smem_of<MODE, R>()}
+    {M, R, search_kernel<MODE, kShortT, R, kLongT, kLongR>, smem_of<MODE, R>(), 0}
 const Entry kEntries[] = {
     SWGB_ENTRY(0, ModePairDb, 8),     SWGB_ENTRY(0, ModePairDb, 12),
     SWGB_ENTRY(0, ModePairDb, 16),    SWGB_ENTRY(0, ModePairDb, 20),
@@ -795,55 +874,65 @@ const Entry kEntries[] = {
     SWGB_ENTRY(1, ModeQueryPair, 12), SWGB_ENTRY(1, ModeQueryPair, 16),
     SWGB_ENTRY(1, ModeQueryPair, 20), SWGB_ENTRY(1, ModeQueryPair, 24),
     SWGB_ENTRY(2, ModeInt32, 16),
-#define SWGB_RING(R) {3, R, search_kernel<ModeRing, kShortT, R, kLongT, kLongR>, 0}
-    SWGB_RING(8), SWGB_RING(12), SWGB_RING(16), SWGB_RING(20), SWGB_RING(24),
+#define SWGB_RING(S, R) {3, R, search_kernel<ModeRing<S>, kShortT, R, kLongT, kLongR>, 0, S}
+    SWGB_RING(1, 8), SWGB_RING(1, 12), SWGB_RING(1, 16), SWGB_RING(1, 20), SWGB_RING(1, 24),
+    SWGB_RING(2, 8), SWGB_RING(2, 12), SWGB_RING(2, 16), SWGB_RING(2, 20), SWGB_RING(2, 24),
 #undef SWGB_RING
 };
 #undef SWGB_ENTRY
 
 // Dynamic shared memory of one launch (the ring grows with the alphabet).
 size_t entry_smem(const Entry& e, uint32_t alphabet) {
-    return e.mode == 3 ? ring_smem_bytes(alphabet) : e.smem;
+    return e.mode == 3 ? ring_smem_bytes(alphabet, e.skew) : e.smem;
 }
+// The largest alphabet an entry serves.
+uint32_t entry_max_alphabet(const Entry& e) { return e.skew == 2 ? kRing2MaxAlphabet : 32; }
 
-const Entry* find_entry(const KernelChoice& kc) {
+// The entry for a choice and alphabet: rings take the two-column skew when its
+// window fits (alphabet <= kRing2MaxAlphabet), else the one-column skew.
+const Entry* find_entry(const KernelChoice& kc, uint32_t alphabet) {
+    const int skew = kc.mode != KernelChoice::kPairRing ? 0 : (alphabet <= kRing2MaxAlphabet ? 2 : 1);
     for (const Entry& e : kEntries)
-        if (e.R == kc.R && e.mode == (int)kc.mode) return &e;
+        if (e.R == kc.R && e.mode == (int)kc.mode && e.skew == skew) return &e;
     return nullptr;
 }
 
 }  // namespace
 
-bool wavefront_supported(const KernelChoice& kc) { return find_entry(kc) != nullptr; }
+bool wavefront_supported(const KernelChoice& kc) { return find_entry(kc, 32) != nullptr; }
 int wavefront_block_threads() { return kThreads; }
 int wavefront_short_units_per_chunk() { return kWarps * (32 / kShortT); }
 
 int wavefront_occupancy(const KernelChoice& kc, int* threads_per_block) {
-    const Entry* e = find_entry(kc);
     if (threads_per_block) *threads_per_block = kThreads;
-    if (!e) return 0;
-    const size_t smem = entry_smem(*e, 32);  // the largest alphabet
-    if (smem > 48 * 1024 &&
-        cudaFuncSetAttribute(e->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-            cudaSuccess)
-        return 0;
+    // every entry the choice may launch, at the largest alphabet it serves
     int blocks = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, e->fn, kThreads, smem) !=
-        cudaSuccess)
-        return 0;
+    for (uint32_t A : {kRing2MaxAlphabet, 32u}) {
+        const Entry* e = find_entry(kc, A);
+        if (!e) return 0;
+        const size_t smem = entry_smem(*e, entry_max_alphabet(*e));
+        if (smem > 48 * 1024 &&
+            cudaFuncSetAttribute(e->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+                cudaSuccess)
+            return 0;
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, e->fn, kThreads, smem) != cudaSuccess)
+            return 0;
+        blocks = std::max(blocks, b);
+    }
     return blocks;
 }
 
 cudaError_t launch_wavefront(const KernelChoice& kc, const WavefrontArgs& a, int grid,
                              cudaStream_t stream) {
-    const Entry* e = find_entry(kc);
+    if (a.alphabet < 1 || a.alphabet > 32) return cudaErrorInvalidValue;
+    const Entry* e = find_entry(kc, a.alphabet);
     if (!e) return cudaErrorInvalidValue;
     if (grid <= 0) return cudaErrorInvalidConfiguration;
-    if (a.alphabet < 1 || a.alphabet > 32) return cudaErrorInvalidValue;
     const size_t smem = entry_smem(*e, a.alphabet);
     if (smem > 48 * 1024) {
         cudaError_t err = cudaFuncSetAttribute(e->fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)entry_smem(*e, 32));
+                                               (int)entry_smem(*e, entry_max_alphabet(*e)));
         if (err != cudaSuccess) return err;
     }
     e->fn<<<grid, kThreads, smem, stream>>>(a);
