@@ -47,11 +47,12 @@ ALU_OPS_PER_CELL = 3.5
 ALU_LANES_PER_CLK_SM = 64     # 32-bit lanes per clock per SM on the integer ALU pipe (4 x 16)
 S16X2_CELLS_PER_LANE = 2      # one 32-bit lane holds two 16-bit DP cells
 PAPER_PHI_GCUPS_MAX = 58.8    # SWAPHI InterSP, one Xeon Phi 5110P, TrEMBL (Section IV.A)
-# DRAM bytes per DP cell of the search kernel (ncu dram__bytes_read + _write on a
-# 600,000-sequence case; profiles/search_kernel_pairdb_600k_ncu.md), valid for the
-# kernel source whose sha256 starts with TRAFFIC_SOURCE.
-TRAFFIC_BYTES_PER_CELL = 0.0277
-TRAFFIC_SOURCE = "10a819ec0d0d5ef1"
+# DRAM bytes per DP cell of the dominant search kernel, the score-profile ring at 24 rows
+# per thread (ncu dram__bytes_read + _write on a 600,000-sequence case;
+# profiles/search_kernel_ring_807x600k_ncu.md), valid for the kernel source whose sha256
+# starts with TRAFFIC_SOURCE.
+TRAFFIC_BYTES_PER_CELL = 0.0186
+TRAFFIC_SOURCE = "98ce66b7fb1686fc"
 
 
 def parse_args():

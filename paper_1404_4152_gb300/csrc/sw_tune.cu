@@ -94,10 +94,23 @@ extern "C" sw_status sw_db_autotune(sw_db* db, const int8_t* matrix, int32_t alp
     bool cached = load_cache(cache_path, key, &t);
     cudaError_t e;
     if (!cached) {
-        // sample: up to 40,000 consecutive sequences from the middle of the shorter bin
+        // sample: up to 40,000 consecutive sequences of the shorter bin centred on its
+        // residue-weighted median (the lengths that carry most of the work)
         const uint64_t short_units = (db->n_tiles - db->n_long_tiles) * kTileSeqs;
         const uint64_t sample = std::min<uint64_t>(short_units, 40000);
-        const uint64_t first = db->n_long_tiles * kTileSeqs + (short_units - sample) / 2;
+        uint64_t centre = db->n_long_tiles;  // tile at the residue median of the short bin
+        {
+            uint64_t total = 0, acc = 0;
+            for (uint64_t u = db->n_long_tiles; u < db->n_tiles; ++u) total += db->tile_len_host[u];
+            for (uint64_t u = db->n_long_tiles; u < db->n_tiles; ++u) {
+                acc += db->tile_len_host[u];
+                if (2 * acc >= total) { centre = u; break; }
+            }
+        }
+        const uint64_t lo = db->n_long_tiles * kTileSeqs;
+        uint64_t first = centre * kTileSeqs > lo + sample / 2 ? centre * kTileSeqs - sample / 2 : lo;
+        if (first + sample > lo + short_units) first = lo + short_units - sample;
+        first &= ~(uint64_t)(kTileSeqs - 1);  // whole tiles, whole pairs
         uint64_t residues = 0;  // padded residues in the sample
         for (uint64_t u = first / kTileSeqs; u < (first + sample + kTileSeqs - 1) / kTileSeqs; ++u)
             residues += (uint64_t)db->tile_len_host[u] * kTileSeqs;
@@ -163,7 +176,7 @@ extern "C" sw_status sw_db_autotune(sw_db* db, const int8_t* matrix, int32_t alp
                 const int occ = std::max(1, wavefront_occupancy(kc, nullptr));
                 const int grid = std::max(1, std::min(db->grid_short, db->nsm * occ));
                 float best = 1e30f;
-                for (int rep = 0; rep < 3; ++rep) {
+                for (int rep = 0; rep < 5; ++rep) {
                     cudaMemsetAsync(db->d_counters, 0, 64, db->stream);
                     cudaEventRecord(e0, db->stream);
                     if ((e = launch_wavefront(kc, a, grid, db->stream)) != cudaSuccess) break;

@@ -445,7 +445,9 @@ struct ModeRing {
 
 constexpr int kRingBlock = 8;      // steps per block = columns built per block
 constexpr int kStageWords = 18;    // per group: 8 boundary entries of (H, E), padded against conflicts
-constexpr uint32_t kMtBytes = kProfileRows * 32;  // fsbt by database code: [33][32 query codes] int8
+// fsbt by database code d: word [k][d] packs fsbt(4k .. 4k+3, d) as int8 (k < 8, d < 33), so
+// threads loading word k for different codes d hit different banks
+constexpr uint32_t kMtBytes = 8 * kProfileRows * 4;
 constexpr uint32_t kRingOffset = kMtBytes + kWarps * 4 * kStageWords * 4;
 // The two-column skew needs a larger window; it keeps two blocks per SM up to this alphabet.
 constexpr uint32_t kRing2MaxAlphabet = 20;
@@ -502,8 +504,9 @@ __device__ __forceinline__ void sts_u64(uint32_t addr, uint2 v) {
 template <int S>
 __device__ __forceinline__ void ring_setup(const WavefrontArgs& a, uint8_t* smem) {
     const uint32_t A = a.alphabet;
-    for (uint32_t idx = threadIdx.x; idx < kProfileRows * 32; idx += kThreads) {
-        const uint32_t d = idx / 32, c = idx % 32;
+    for (uint32_t idx = threadIdx.x; idx < 8 * kProfileRows * 4; idx += kThreads) {
+        const uint32_t k = idx / (kProfileRows * 4), d = (idx / 4) % kProfileRows;
+        const uint32_t c = 4 * k + idx % 4;
         smem[idx] = (uint8_t)((c < A && d < A) ? a.matrix[c * A + d] : 0);
     }
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -544,7 +547,7 @@ __device__ __forceinline__ void process_chunk_ring(const WavefrontArgs& a, const
     const uint32_t smem_s = (uint32_t)__cvta_generic_to_shared(smem);
     const uint32_t ring_s = smem_s + kRingOffset + (uint32_t)warp * (A + 1) * kCodeBytes + g * 4;
     const uint32_t stage_s = smem_s + kMtBytes + (uint32_t)(warp * 4 + g) * kStageWords * 4;
-    const uint4* const mt = reinterpret_cast<const uint4*>(smem);
+    const uint32_t* const mt = reinterpret_cast<const uint32_t*>(smem);
 
     const V vbeta = Lane::splat(-a.beta);
     const V valpha = Lane::splat(-a.alpha);
@@ -624,10 +627,8 @@ __device__ __forceinline__ void process_chunk_ring(const WavefrontArgs& a, const
                 const uint32_t j = s0 + bcol;
                 uint32_t pc = kPadPair;
                 if (j < L) pc = *reinterpret_cast<const uint16_t*>(stream + (size_t)(j >> 2) * 32 + (j & 3) * 2);
-                const uint4 a0 = mt[(pc & 0xffu) * 2], a1 = mt[(pc & 0xffu) * 2 + 1];
-                const uint4 b0 = mt[(pc >> 8) * 2], b1 = mt[(pc >> 8) * 2 + 1];
-                const uint32_t wa[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-                const uint32_t wb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+                const uint32_t* const ma = mt + (pc & 0xffu);
+                const uint32_t* const mb = mt + (pc >> 8);
                 bool dup;
                 const uint32_t at = ring_s + col_off(j, dup);
                 if constexpr (kSplit == 1) {
@@ -635,12 +636,13 @@ __device__ __forceinline__ void process_chunk_ring(const WavefrontArgs& a, const
                     for (int k = 0; k < 8; ++k) {
                         if (4u * k >= A) break;
                         const bool whole = 4u * k + 4 <= A;  // uniform: no per-code test
+                        const uint32_t wa = ma[k * kProfileRows], wb = mb[k * kProfileRows];
 #pragma unroll
                         for (int b = 0; b < 4; ++b) {
                             const uint32_t c = 4u * k + b;
                             if (whole || c < A) {
-                                const uint32_t v = prmt(wa[k], wb[k], b | ((8u | b) << 4) |
-                                                                          ((4u + b) << 8) | ((12u + b) << 12));
+                                const uint32_t v = prmt(wa, wb, b | ((8u | b) << 4) |
+                                                                  ((4u + b) << 8) | ((12u + b) << 12));
                                 sts_u32(at + c * kCodeBytes, v);
                                 if (dup) sts_u32(at + c * kCodeBytes + W * kSlot, v);
                             }
@@ -652,8 +654,9 @@ __device__ __forceinline__ void process_chunk_ring(const WavefrontArgs& a, const
                     for (int k = 0; k < 8; ++k) {
                         if (4u * k >= A) break;
                         const uint32_t c = 4u * k + bq;
+                        const uint32_t wa = ma[k * kProfileRows], wb = mb[k * kProfileRows];
                         if (c < A) {
-                            const uint32_t v = prmt(wa[k], wb[k], bsel);
+                            const uint32_t v = prmt(wa, wb, bsel);
                             sts_u32(at + c * kCodeBytes, v);
                             if (dup) sts_u32(at + c * kCodeBytes + W * kSlot, v);
                         }
