@@ -17,6 +17,11 @@ included). GCUPS = sum(|query|) * sum(|db sequence|) / seconds.
              algorithmic ALU lane-operations / its mean launch time, against the
              ALU-pipe peak at the SM clock sampled during the run.
   cpu_baseline  the CPU oracle on a bounded sample of the same workload.
+  batched    256 queries against 1,000,000 sequences in one graph-captured launch.
+  served     the continuous-batching server over 20,000,000 resident sequences,
+             Poisson arrivals: p50 / p99 latency and sustained GCUPS per rate.
+  long_sequences  a 5,478-residue query against 100,000 long sequences (the
+             warp-per-pair kernel) and the same scaled x3 (int32 rescoring).
 
 --impl reference times the CPU oracle itself as the reference arm.
 Under torchrun each rank searches its own database shard (weak scaling); the
@@ -74,6 +79,8 @@ def parse_args():
     p.add_argument("--serve-rates", default="1.0",
                    help="comma-separated Poisson arrival rates (queries/s); empty skips serving")
     p.add_argument("--serve-arrivals", type=int, default=16)
+    p.add_argument("--long-steps", type=int, default=2,
+                   help="timed searches of the long-sequence workloads (config 4 and 4b; 0 skips)")
     p.add_argument("--no-tune", action="store_true")
     return p.parse_args()
 
@@ -220,6 +227,57 @@ def run_batched(args, sw, torch, dev, rank):
                         f"persistent launch per step",
             "value": cells / (ms / 1e3) / 1e9, "unit": "GCUPS", "steps": args.batch_steps,
             "ms_per_step": ms / args.batch_steps, "gpu_launches": int(prof["launches"])}
+
+
+def run_long(args, sw, torch, dev, rank):
+    """Long sequences: a 5,478-residue query vs 100,000 sequences (mean 2,000, up to 35,000;
+    17 % above 3,000 residues go to the warp-per-pair kernel), with 1,000 planted
+    near-duplicates; 4b scales matrix and penalties by 3 so the planted pairs pass the
+    16-bit range and are rescored in int32. GCUPS and the per-phase device time."""
+    out = []
+    for scale in (1, 3):
+        w = synth.config4(seed=1408 + 1000 * rank, scale=scale)
+        db = sw.sw_db_load(w.residues, w.offsets, alphabet=20, long_threshold=3000,
+                           flags=sw.SW_DB_FLAG_PROFILE)
+        q = w.queries[0]
+        n, k = w.n_seqs, w.top_k
+        d_q = torch.from_numpy(q).to(dev)
+        d_m = torch.from_numpy(w.matrix.copy()).to(dev)
+        d_s = torch.empty(n, dtype=torch.int32, device=dev)
+        d_ts = torch.empty(k, dtype=torch.int32, device=dev)
+        d_ti = torch.empty(k, dtype=torch.int64, device=dev)
+        stream = torch.cuda.Stream(device=dev)
+
+        def step():
+            sw.sw_search_device(db, d_q, q.size, d_m, w.alpha, w.beta, k, d_s, d_ts, d_ti, stream)
+
+        step()
+        stream.synchronize()
+        sw.sw_db_reset_profile(db)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.long_steps):
+            step()
+        e1.record(stream)
+        stream.synchronize()
+        ms = e0.elapsed_time(e1)
+        prof = sw.sw_db_get_profile(db)
+        info = db.info()
+        planted = w.notes["planted"]
+        saturated = int((d_s.cpu().numpy()[planted] > 32767).sum())
+        db.free()
+        cells = q.size * w.db_residues * args.long_steps
+        out.append({"workload": f"{w.name}: one {q.size}-residue query vs {n:,} sequences "
+                                f"({w.db_residues / 1e6:.0f} M aa, {info['n_long']:,} above 3,000), "
+                                f"{len(planted)} planted near-duplicates"
+                                + (", matrix and penalties x3" if scale > 1 else ""),
+                    "value": cells / (ms / 1e3) / 1e9, "unit": "GCUPS", "steps": args.long_steps,
+                    "ms_per_step": ms / args.long_steps,
+                    "phases_ms": {p: v["ms"] / args.long_steps for p, v in prof["phases"].items()},
+                    "gpu_launches": int(prof["launches"]),
+                    "planted_above_16_bit": saturated})
+    return out
 
 
 def run_served(args, sw, rank):
@@ -474,6 +532,8 @@ def run_ours(args):
         batched = run_batched(args, sw, torch, dev, rank)
         batched["vs_plain"] = batched["value"] / (value / world)
 
+    long_seqs = run_long(args, sw, torch, dev, rank) if args.long_steps > 0 else None
+
     cpu = None
     if not args.no_cpu and world == 1 and rank == 0:
         threads = os.cpu_count() or 1
@@ -492,6 +552,7 @@ def run_ours(args):
         "phases_ms": {p: ph[p]["ms"] for p in ph},
         "batched": batched,
         "served": served,
+        "long_sequences": long_seqs,
         "sharded_top_k": merged,
         "tuning": tuning,
         "per_query": per_query,
