@@ -486,6 +486,7 @@ def run_ours(args):
     traffic = TRAFFIC_BYTES_PER_CELL * cells_per_launch if same_kernel else None
     roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "Gop/s",
                 "frac": achieved / peak, "traffic": traffic,
+                "dram_gbs": traffic / (mean_ms / 1e3) / 1e9 if traffic else None,
                 "per_unit": f"{ALU_OPS_PER_CELL} integer ALU lane-ops per DP cell (minimum); "
                             f"{cells_per_launch:.4g} cells per launch, mean launch {mean_ms:.2f} ms",
                 "peak_basis": f"{nsm} SMs x {sm_mhz:.0f} MHz (sampled) x {ALU_LANES_PER_CLK_SM} ALU "

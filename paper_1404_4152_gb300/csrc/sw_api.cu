@@ -108,9 +108,6 @@ void release(sw_db* db) {
     for (auto& a : db->allocs) db_free(db, a.first, a.second);
     db->allocs.clear();
     if (db->stream) cudaStreamDestroy(db->stream);
-    if (db->stream_long) cudaStreamDestroy(db->stream_long);
-    if (db->ev_fork) cudaEventDestroy(db->ev_fork);
-    if (db->ev_join) cudaEventDestroy(db->ev_join);
     if (db->ev_t0) cudaEventDestroy(db->ev_t0);
     if (db->ev_t1) cudaEventDestroy(db->ev_t1);
     if (db->h_pinned) cudaFreeHost(db->h_pinned);
@@ -187,9 +184,6 @@ extern "C" sw_status sw_db_load(const uint8_t* residues, const uint64_t* offsets
     }
     cudaError_t e;
     if ((e = cudaStreamCreateWithFlags(&db->stream, cudaStreamNonBlocking)) != cudaSuccess ||
-        (e = cudaStreamCreateWithFlags(&db->stream_long, cudaStreamNonBlocking)) != cudaSuccess ||
-        (e = cudaEventCreateWithFlags(&db->ev_fork, cudaEventDisableTiming)) != cudaSuccess ||
-        (e = cudaEventCreateWithFlags(&db->ev_join, cudaEventDisableTiming)) != cudaSuccess ||
         (e = cudaEventCreate(&db->ev_t0)) != cudaSuccess ||
         (e = cudaEventCreate(&db->ev_t1)) != cudaSuccess) {
         sw_status st = cuda_fail(e, "sw_db_load: stream/event creation");

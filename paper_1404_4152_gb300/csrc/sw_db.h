@@ -51,9 +51,8 @@ struct sw_db {
     uint32_t flags = 0;
     int nsm = 0;
 
-    cudaStream_t stream = nullptr;       // the library's own stream (host-buffer calls)
-    cudaStream_t stream_long = nullptr;  // side stream for the long-sequence kernel
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_t0 = nullptr, ev_t1 = nullptr;
+    cudaStream_t stream = nullptr;  // the library's own stream (host-buffer calls)
+    cudaEvent_t ev_t0 = nullptr, ev_t1 = nullptr;
 
     // length-sorted tiles (descending length); tiles [0, n_long_tiles) hold the
     // sequences above long_threshold
@@ -65,7 +64,6 @@ struct sw_db {
     uint32_t* d_tile_len = nullptr;
     uint32_t* d_sorted = nullptr;  // sorted position -> original index
     int32_t* d_scores = nullptr;   // internal score row (original order)
-    uint32_t* d_flags = nullptr;   // unused
     uint2* d_flags2 = nullptr;     // (query row, sorted position) rescored in int32
     uint32_t* d_misc = nullptr;
 
