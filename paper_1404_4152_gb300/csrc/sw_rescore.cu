@@ -9,7 +9,8 @@
 // query rows per lane (512 rows per pass), the scoring matrix in shared
 // memory and each lane's query codes for the pass in registers, so a score
 // is one shared-memory load per cell. The (H, E) row between passes goes
-// through the warp's scratch row, as in the search kernels.
+// through the warp's scratch row, as in the search kernels; lane 0 loads the
+// sequence codes and that row one 4-column block ahead.
 #include <cuda_runtime.h>
 #include <cstdint>
 
@@ -53,10 +54,11 @@ __global__ void __launch_bounds__(kThreads) rescore_kernel(const RescoreArgs a) 
         const uint32_t m = a.qoff ? a.qlen[q] : a.single_qlen;
         const uint64_t tile = sp / kTileSeqs;
         const uint32_t L = a.tile_len[tile];
-        const uint8_t* stream =
-            a.tile_data + a.tile_off[tile] + ((sp >> 1) & (kTilePairs - 1)) * 8 + (sp & 1);
+        const uint8_t* stream = a.tile_data + a.tile_off[tile] + ((sp >> 1) & (kTilePairs - 1)) * 8;
         const uint32_t P = (m + kRows - 1) / kRows;
-        const uint32_t steps = L + kT - 1;
+        const uint32_t steps = (L + kT - 1 + 3) & ~3u;
+        const uint32_t blocks_real = L / 4;  // 4-column blocks of the sequence (L is a multiple of 4)
+        const uint32_t byte_sel = (uint32_t)(sp & 1);
         int32_t best = 0;
         for (uint32_t p = 0; p < P; ++p) {
             // this lane's query codes for the pass (pad code past the query end)
@@ -74,40 +76,64 @@ __global__ void __launch_bounds__(kThreads) rescore_kernel(const RescoreArgs a) 
             for (int l = 0; l < kR; ++l) { Hl[l] = 0; Fr[l] = 0; }
             int32_t hb_out = 0, eb_out = 0, hdiag0 = 0;
             uint32_t code_out = kPadCode;
-            for (uint32_t s = 0; s < steps; ++s) {
-                const int j = (int)s - t;
-                int32_t h_in = (int32_t)__shfl_up_sync(0xffffffffu, (uint32_t)hb_out, 1);
-                int32_t e_in = (int32_t)__shfl_up_sync(0xffffffffu, (uint32_t)eb_out, 1);
-                uint32_t code = __shfl_up_sync(0xffffffffu, code_out, 1);
-                if (t == 0) {
-                    const bool real = j < (int)L;
-                    code = real ? (uint32_t)stream[(j >> 2) * 32 + (j & 3) * 2] : kPadCode;
-                    if (code > kPadCode) code = kPadCode;
-                    h_in = 0;
-                    e_in = 0;
-                    if (p > 0 && real) {
-                        const uint2 v = bin[j];
-                        h_in = (int32_t)v.x;
-                        e_in = (int32_t)v.y;
+            // lane 0's codes (a word of 4 columns x 2 sequences) and boundary entries,
+            // loaded one 4-column block ahead
+            const uint2 kPadW = make_uint2(0x20202020u, 0x20202020u);
+            uint2 wq = kPadW;
+            uint4 bq0 = make_uint4(0, 0, 0, 0), bq1 = make_uint4(0, 0, 0, 0);
+            if (t == 0 && blocks_real > 0) {
+                wq = *reinterpret_cast<const uint2*>(stream);
+                if (p > 0) {
+                    bq0 = reinterpret_cast<const uint4*>(bin)[0];
+                    bq1 = reinterpret_cast<const uint4*>(bin)[1];
+                }
+            }
+            for (uint32_t s0 = 0; s0 < steps; s0 += 4) {
+                uint2 wn = kPadW;
+                uint4 bn0 = make_uint4(0, 0, 0, 0), bn1 = make_uint4(0, 0, 0, 0);
+                const uint32_t nb = (s0 >> 2) + 1;
+                if (t == 0 && nb < blocks_real) {
+                    wn = *reinterpret_cast<const uint2*>(stream + (size_t)nb * 32);
+                    if (p > 0) {
+                        bn0 = reinterpret_cast<const uint4*>(bin + s0 + 4)[0];
+                        bn1 = reinterpret_cast<const uint4*>(bin + s0 + 4)[1];
                     }
                 }
-                code_out = code;
-                int32_t diag = hdiag0, E = e_in;
 #pragma unroll
-                for (int l = 0; l < kR; ++l) {
-                    const int32_t sc = sM[qc[l] + code];
-                    const int32_t H = LaneS32::max3_relu(diag + sc, E, Fr[l]);
-                    diag = Hl[l];
-                    Hl[l] = H;
-                    const int32_t hb = H - a.beta;
-                    E = max(E - a.alpha, hb);
-                    Fr[l] = max(Fr[l] - a.alpha, hb);
-                    best = max(best, H);
+                for (int k = 0; k < 4; ++k) {
+                    int32_t h_in = (int32_t)__shfl_up_sync(0xffffffffu, (uint32_t)hb_out, 1);
+                    int32_t e_in = (int32_t)__shfl_up_sync(0xffffffffu, (uint32_t)eb_out, 1);
+                    uint32_t code = __shfl_up_sync(0xffffffffu, code_out, 1);
+                    if (t == 0) {
+                        const uint32_t w = (k < 2) ? wq.x : wq.y;
+                        code = (w >> (16 * (k & 1) + 8 * byte_sel)) & 0xffu;
+                        if (code > kPadCode) code = kPadCode;
+                        const uint4& bq = (k < 2) ? bq0 : bq1;
+                        h_in = (int32_t)((k & 1) ? bq.z : bq.x);
+                        e_in = (int32_t)((k & 1) ? bq.w : bq.y);
+                    }
+                    code_out = code;
+                    int32_t diag = hdiag0, E = e_in;
+#pragma unroll
+                    for (int l = 0; l < kR; ++l) {
+                        const int32_t sc = sM[qc[l] + code];
+                        const int32_t H = LaneS32::max3_relu(diag + sc, E, Fr[l]);
+                        diag = Hl[l];
+                        Hl[l] = H;
+                        const int32_t hb = H - a.beta;
+                        E = max(E - a.alpha, hb);
+                        Fr[l] = max(Fr[l] - a.alpha, hb);
+                        best = max(best, H);
+                    }
+                    hb_out = Hl[kR - 1];
+                    eb_out = E;
+                    hdiag0 = h_in;
+                    if (t == kT - 1 && p + 1 < P)  // column s - 31, at entry kT + that >= 1
+                        bout[(int)(s0 + k) - (kT - 1)] = make_uint2((uint32_t)hb_out, (uint32_t)eb_out);
                 }
-                hb_out = Hl[kR - 1];
-                eb_out = E;
-                hdiag0 = h_in;
-                if (t == kT - 1 && p + 1 < P) bout[j] = make_uint2((uint32_t)hb_out, (uint32_t)eb_out);
+                wq = wn;
+                bq0 = bn0;
+                bq1 = bn1;
             }
         }
 #pragma unroll
