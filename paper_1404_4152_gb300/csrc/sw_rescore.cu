@@ -4,13 +4,21 @@
 // The paper keeps scores exact by computing in 32-bit lanes throughout
 // (Section III); the packed 16-bit kernels here are exact below a threshold
 // and hand every pair that reached it to this kernel, which evaluates
-// recurrence (1) again in int32. Such pairs are rare (under BLOSUM62 a score
-// must pass ~32,700), so this kernel favours simplicity: a warp per pair, 16
-// query rows per lane (512 rows per pass), the scoring matrix in shared
-// memory and each lane's query codes for the pass in registers, so a score
-// is one shared-memory load per cell. The (H, E) row between passes goes
-// through the warp's scratch row, as in the search kernels; lane 0 loads the
-// sequence codes and that row one 4-column block ahead.
+// recurrence (1) again in int32. Such pairs are the highest-scoring, hence
+// long, ones, and often few, so a whole block works on one pair: a wavefront
+// of warps over bands of query rows.
+//
+// Each warp owns bands of kBand = 32 lanes x kR rows (bands w, w + 8, ...); in
+// a band its lanes run the usual lane wavefront (lane t on column s - t at
+// step s) with the scoring matrix in shared memory. Time is cut into
+// super-steps of kC lane-steps separated by __syncthreads: at super-step k,
+// warp w works on block g = k - 2w of its band sequence (band w + 8 (g / NBP),
+// column block g % NBP), so warp w + 1 runs two blocks (at least 64 columns,
+// more than the 31-column lane skew) behind warp w and reads the rows it
+// needs from warp w's shared-memory ring of bottom rows. Warp 7 hands its
+// bottom rows to warp 0's next band through a global scratch row; NBP >= 16
+// column blocks per band keeps that row written before warp 0 reads it. No
+// thread waits on another except at the block barriers.
 #include <cuda_runtime.h>
 #include <cstdint>
 
@@ -24,28 +32,39 @@ namespace {
 constexpr int kWarps = 8;
 constexpr int kThreads = kWarps * 32;
 constexpr int kT = 32;
-constexpr int kR = 16;
-constexpr int kRows = kT * kR;
-constexpr int kM = kProfileRows;  // matrix staged as [33][33], pad row/column zero
+constexpr int kR = 8;
+constexpr int kBand = kT * kR;      // query rows per band
+constexpr int kC = 64;              // lane-steps per super-step
+constexpr int kRing = 4 * kC;       // bottom-row entries kept per warp
+constexpr int kLag = 2;             // blocks between consecutive warps
+constexpr int kMinNBP = 16;         // > kLag * (kWarps - 1) + 1
+constexpr int kM = kProfileRows;    // matrix staged as [33][33], pad row/column zero
+
+struct Smem {
+    int32_t M[kM * kM];
+    uint2 ring[kWarps][kRing];      // (H, E) of each warp's bottom row, by column
+    uint2 top0[kC];                 // warp 0's top row for the current block
+    uint8_t code[kWarps][kC];       // each warp's database codes for the current block
+    int32_t best[kWarps];
+    uint32_t entry;
+};
 
 __global__ void __launch_bounds__(kThreads) rescore_kernel(const RescoreArgs a) {
-    __shared__ int32_t sM[kM * kM];
+    __shared__ Smem sm;
     for (uint32_t i = threadIdx.x; i < kM * kM; i += kThreads) {
         const uint32_t r = i / kM, c = i % kM;
-        sM[i] = (r < a.alphabet && c < a.alphabet) ? (int32_t)a.matrix[r * a.alphabet + c] : 0;
+        sm.M[i] = (r < a.alphabet && c < a.alphabet) ? (int32_t)a.matrix[r * a.alphabet + c] : 0;
     }
-    __syncthreads();
 
-    const int warp = threadIdx.x >> 5, t = threadIdx.x & 31;
-    const uint64_t slot = (uint64_t)blockIdx.x * kWarps + warp;
-    uint2* const bnd0 = a.boundary + slot * a.bstride;
-    const uint64_t half = a.bstride / 2;
+    const int w = threadIdx.x >> 5, t = threadIdx.x & 31;
+    uint2* const row7 = a.boundary + (uint64_t)blockIdx.x * a.bstride;  // warp 7 -> warp 0
     const uint32_t count = min(*a.count, a.cap);
 
     for (;;) {
-        uint32_t e = 0;
-        if (t == 0) e = atomicAdd(a.work_counter, 1u);
-        e = __shfl_sync(0xffffffffu, e, 0);
+        __syncthreads();  // the previous pair is finished with the shared state
+        if (threadIdx.x == 0) sm.entry = atomicAdd(a.work_counter, 1u);
+        __syncthreads();
+        const uint32_t e = sm.entry;
         if (e >= count) break;
         const uint2 ent = a.list[e];
         const uint32_t q = ent.x;
@@ -54,69 +73,79 @@ __global__ void __launch_bounds__(kThreads) rescore_kernel(const RescoreArgs a) 
         const uint32_t m = a.qoff ? a.qlen[q] : a.single_qlen;
         const uint64_t tile = sp / kTileSeqs;
         const uint32_t L = a.tile_len[tile];
-        const uint8_t* stream = a.tile_data + a.tile_off[tile] + ((sp >> 1) & (kTilePairs - 1)) * 8;
-        const uint32_t P = (m + kRows - 1) / kRows;
-        const uint32_t steps = (L + kT - 1 + 3) & ~3u;
-        const uint32_t blocks_real = L / 4;  // 4-column blocks of the sequence (L is a multiple of 4)
-        const uint32_t byte_sel = (uint32_t)(sp & 1);
+        const uint8_t* stream =
+            a.tile_data + a.tile_off[tile] + ((sp >> 1) & (kTilePairs - 1)) * 8 + (sp & 1);
+        const uint32_t nband = (m + kBand - 1) / kBand;
+        const uint32_t ns = (L + kT - 1 + kC - 1) / kC;  // blocks per band
+        const uint32_t nbp = ns > (uint32_t)kMinNBP ? ns : (uint32_t)kMinNBP;
+        const uint32_t rounds = (nband + kWarps - 1) / kWarps;
+        const uint32_t K = kLag * (kWarps - 1) + nbp * rounds;
+
         int32_t best = 0;
-        for (uint32_t p = 0; p < P; ++p) {
-            // this lane's query codes for the pass (pad code past the query end)
-            uint32_t qc[kR];
-#pragma unroll
-            for (int l = 0; l < kR; ++l) {
-                const uint32_t row = p * kRows + t * kR + l;
-                uint32_t c = row < m ? (uint32_t)qs[row] : kPadCode;
-                qc[l] = (c < a.alphabet ? c : kPadCode) * kM;
+        uint32_t qc[kR];
+        int32_t Hl[kR], Fr[kR];
+        int32_t hb_out = 0, eb_out = 0, hdiag0 = 0;
+        uint32_t code_out = kPadCode;
+        for (uint32_t k = 0; k < K; ++k) {
+            const int64_t g = (int64_t)k - kLag * w;
+            bool active = false;
+            uint32_t round = 0, b = 0, band = 0;
+            if (g >= 0) {
+                round = (uint32_t)g / nbp;
+                b = (uint32_t)g % nbp;
+                band = (uint32_t)w + kWarps * round;
+                active = band < nband && b < ns;
             }
-            const uint2* bin = bnd0 + (p & 1) * half + kT;
-            uint2* bout = bnd0 + ((p + 1) & 1) * half + kT;
-            int32_t Hl[kR], Fr[kR];
+            if (active) {
+                if (b == 0) {  // a new band: this lane's query codes, empty rows
 #pragma unroll
-            for (int l = 0; l < kR; ++l) { Hl[l] = 0; Fr[l] = 0; }
-            int32_t hb_out = 0, eb_out = 0, hdiag0 = 0;
-            uint32_t code_out = kPadCode;
-            // lane 0's codes (a word of 4 columns x 2 sequences) and boundary entries,
-            // loaded one 4-column block ahead
-            const uint2 kPadW = make_uint2(0x20202020u, 0x20202020u);
-            uint2 wq = kPadW;
-            uint4 bq0 = make_uint4(0, 0, 0, 0), bq1 = make_uint4(0, 0, 0, 0);
-            if (t == 0 && blocks_real > 0) {
-                wq = *reinterpret_cast<const uint2*>(stream);
-                if (p > 0) {
-                    bq0 = reinterpret_cast<const uint4*>(bin)[0];
-                    bq1 = reinterpret_cast<const uint4*>(bin)[1];
-                }
-            }
-            for (uint32_t s0 = 0; s0 < steps; s0 += 4) {
-                uint2 wn = kPadW;
-                uint4 bn0 = make_uint4(0, 0, 0, 0), bn1 = make_uint4(0, 0, 0, 0);
-                const uint32_t nb = (s0 >> 2) + 1;
-                if (t == 0 && nb < blocks_real) {
-                    wn = *reinterpret_cast<const uint2*>(stream + (size_t)nb * 32);
-                    if (p > 0) {
-                        bn0 = reinterpret_cast<const uint4*>(bin + s0 + 4)[0];
-                        bn1 = reinterpret_cast<const uint4*>(bin + s0 + 4)[1];
+                    for (int l = 0; l < kR; ++l) {
+                        const uint32_t row = band * kBand + t * kR + l;
+                        const uint32_t c = row < m ? (uint32_t)qs[row] : kPadCode;
+                        qc[l] = (c < a.alphabet ? c : kPadCode) * kM;
+                        Hl[l] = 0;
+                        Fr[l] = 0;
                     }
+                    hb_out = eb_out = hdiag0 = 0;
+                    code_out = kPadCode;
                 }
+                // lane 0's inputs for this block: database codes and, for warp 0 after
+                // the first round, warp 7's bottom row of the band above
+                const uint32_t c0 = b * kC;
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
+                for (int h = 0; h < 2; ++h) {
+                    const uint32_t j = c0 + (uint32_t)t + 32u * h;
+                    uint32_t c = kPadCode;
+                    if (j < L) {
+                        c = stream[(size_t)(j >> 2) * 32 + (j & 3) * 2];
+                        if (c > kPadCode) c = kPadCode;
+                    }
+                    sm.code[w][t + 32 * h] = (uint8_t)c;
+                    if (w == 0)
+                        sm.top0[t + 32 * h] = (band > 0 && j < L) ? row7[j] : make_uint2(0, 0);
+                }
+                __syncwarp();
+                const uint32_t ring_base = round * nbp * kC;  // ring index of column 0 in this round
+                for (uint32_t s = 0; s < (uint32_t)kC; ++s) {
+                    const uint32_t sigma = c0 + s;  // lane 0's column
                     int32_t h_in = (int32_t)__shfl_up_sync(0xffffffffu, (uint32_t)hb_out, 1);
                     int32_t e_in = (int32_t)__shfl_up_sync(0xffffffffu, (uint32_t)eb_out, 1);
                     uint32_t code = __shfl_up_sync(0xffffffffu, code_out, 1);
                     if (t == 0) {
-                        const uint32_t w = (k < 2) ? wq.x : wq.y;
-                        code = (w >> (16 * (k & 1) + 8 * byte_sel)) & 0xffu;
-                        if (code > kPadCode) code = kPadCode;
-                        const uint4& bq = (k < 2) ? bq0 : bq1;
-                        h_in = (int32_t)((k & 1) ? bq.z : bq.x);
-                        e_in = (int32_t)((k & 1) ? bq.w : bq.y);
+                        code = sm.code[w][s];
+                        uint2 top = make_uint2(0, 0);
+                        if (w == 0)
+                            top = sm.top0[s];
+                        else if (sigma < L)
+                            top = sm.ring[w - 1][(ring_base + sigma) % kRing];
+                        h_in = (int32_t)top.x;
+                        e_in = (int32_t)top.y;
                     }
                     code_out = code;
                     int32_t diag = hdiag0, E = e_in;
 #pragma unroll
                     for (int l = 0; l < kR; ++l) {
-                        const int32_t sc = sM[qc[l] + code];
+                        const int32_t sc = sm.M[qc[l] + code];
                         const int32_t H = LaneS32::max3_relu(diag + sc, E, Fr[l]);
                         diag = Hl[l];
                         Hl[l] = H;
@@ -128,20 +157,28 @@ __global__ void __launch_bounds__(kThreads) rescore_kernel(const RescoreArgs a) 
                     hb_out = Hl[kR - 1];
                     eb_out = E;
                     hdiag0 = h_in;
-                    if (t == kT - 1 && p + 1 < P)  // column s - 31, at entry kT + that >= 1
-                        bout[(int)(s0 + k) - (kT - 1)] = make_uint2((uint32_t)hb_out, (uint32_t)eb_out);
+                    const int64_t j = (int64_t)sigma - (kT - 1);  // lane 31's column
+                    if (t == kT - 1 && j >= 0 && j < (int64_t)L && band + 1 < nband) {
+                        const uint2 v = make_uint2((uint32_t)hb_out, (uint32_t)eb_out);
+                        if (w + 1 < kWarps)
+                            sm.ring[w][(ring_base + (uint32_t)j) % kRing] = v;
+                        else
+                            row7[j] = v;
+                    }
                 }
-                wq = wn;
-                bq0 = bn0;
-                bq1 = bn1;
             }
+            __syncthreads();  // this block's rows are visible to the next warp
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1)
             best = max(best, (int32_t)__shfl_xor_sync(0xffffffffu, (uint32_t)best, o));
-        if (t == 0) {
+        if (t == 0) sm.best[w] = best;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int32_t v = 0;
+            for (int i = 0; i < kWarps; ++i) v = max(v, sm.best[i]);
             const uint32_t id = a.sorted_ids[sp];
-            if (id != 0xffffffffu) a.scores[(uint64_t)q * a.score_stride + id] = best;
+            if (id != 0xffffffffu) a.scores[(uint64_t)q * a.score_stride + id] = v;
         }
     }
 }

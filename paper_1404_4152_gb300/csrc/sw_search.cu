@@ -29,8 +29,8 @@ using namespace swgb;
 namespace {
 
 constexpr int kTopkBlocks = 256;
-constexpr int kRescoreBlocksPerSm = 2;
-constexpr uint64_t kRescoreScratch = 512ull << 20;
+constexpr int kRescoreBlocksPerSm = 4;
+constexpr uint64_t kRescoreScratch = 256ull << 20;
 
 const int kShortR[] = {8, 12, 16, 20, 24};
 
@@ -168,18 +168,17 @@ sw_status sw_db_prepare_search(sw_db* db) {
                            "boundary rows (long)")))
             return st;
     }
-    // rescoring: up to two blocks per SM, as many as 512 MiB of scratch rows allow
+    // rescoring: one block per pair, up to kRescoreBlocksPerSm per SM, each with one
+    // scratch row (bstride entries), as many as kRescoreScratch bytes allow
     db->bstride_rescore = bstride_for(std::max(4u, (db->max_len + 3u) & ~3u));
     {
-        const uint64_t per_block =
-            (uint64_t)(rescore_block_threads() / 32) * db->bstride_rescore * sizeof(uint2);
+        const uint64_t per_block = db->bstride_rescore * sizeof(uint2);
         const uint64_t fit = ((uint64_t)kRescoreScratch) / std::max<uint64_t>(per_block, 1);
         db->grid_rescore = (int)std::max<uint64_t>(
             1, std::min<uint64_t>(fit, (uint64_t)db->nsm * kRescoreBlocksPerSm));
     }
     if ((st = db_alloc(db, (void**)&db->d_bnd_rescore,
-                       (uint64_t)db->grid_rescore * (rescore_block_threads() / 32) *
-                           db->bstride_rescore * sizeof(uint2),
+                       (uint64_t)db->grid_rescore * db->bstride_rescore * sizeof(uint2),
                        "boundary rows (rescoring)")))
         return st;
     if ((st = db_alloc(db, (void**)&db->d_flags2, db->n_seqs * sizeof(uint2), "rescoring list")))
