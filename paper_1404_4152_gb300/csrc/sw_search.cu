@@ -13,6 +13,7 @@
 // chunk, query pair), and is replayed from a captured CUDA graph when the same
 // batch shape is searched again.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <chrono>
@@ -108,24 +109,37 @@ cudaEvent_t take_event(sw_db* db) {
 }
 
 // Brackets one phase with events when the handle is profiled.
+// Also an NVTX range named after the phase on the host thread that enqueues it (for
+// timeline tools; free when none is attached).
 struct PhaseTimer {
     sw_db* db;
     int phase;
     cudaStream_t st;
     uint64_t cells;
     cudaEvent_t a = nullptr;
+    bool open = true;
     PhaseTimer(sw_db* d, int p, cudaStream_t s, uint64_t c) : db(d), phase(p), st(s), cells(c) {
+        static const char* const kNames[4] = {"sw.wavefront", "sw.rescore_int32", "sw.topk",
+                                              "sw.batch"};
+        nvtxRangePushA(kNames[p & 3]);
         if (db->flags & SW_DB_FLAG_PROFILE) {
             a = take_event(db);
             cudaEventRecord(a, st);
         }
     }
     void done() {
+        if (open) {
+            nvtxRangePop();
+            open = false;
+        }
         if (!a) return;
         cudaEvent_t b = take_event(db);
         cudaEventRecord(b, st);
         db->pending.push_back({phase, a, b, cells});
         a = nullptr;
+    }
+    ~PhaseTimer() {
+        if (open) nvtxRangePop();
     }
 };
 
