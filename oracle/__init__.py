@@ -52,6 +52,8 @@ def _declare(lib):
     lib.oracle_scores.restype = ctypes.c_int
     lib.oracle_top_k.argtypes = [p, u64, u32, p, p, p]
     lib.oracle_top_k.restype = ctypes.c_int
+    lib.oracle_sw_align.argtypes = [p, u32, p, u32, p, u32, i32, i32, p, p, u32, p]
+    lib.oracle_sw_align.restype = ctypes.c_int
     return lib
 
 
@@ -127,3 +129,21 @@ def search(query, residues, offsets, matrix, alpha: int, beta: int, k: int,
     s = scores(query, residues, offsets, matrix, alpha, beta, nthreads=nthreads, lib=lib)
     ts, ti = top_k(s, k, lib=lib)
     return s, ts, ti
+
+
+def align(q, d, matrix, alpha: int, beta: int, lib=None):
+    """One optimal local alignment (the oracle's traceback): a dict with score, the 0-based
+    half-open query and database ranges and the op string ('M', 'I', 'D')."""
+    lib = lib or load()
+    q, d = _u8(q), _u8(d)
+    m, A = _matrix(matrix)
+    out = np.zeros(5, dtype=np.int32)
+    cap = int(q.size + d.size + 1)
+    ops = ctypes.create_string_buffer(cap)
+    n_ops = ctypes.c_uint32(0)
+    rc = lib.oracle_sw_align(_ptr(q), q.size, _ptr(d), d.size, _ptr(m), A, int(alpha), int(beta),
+                             _ptr(out), ops, cap, ctypes.byref(n_ops))
+    if rc != 0:
+        raise RuntimeError("oracle_sw_align failed")
+    return {"score": int(out[0]), "q_begin": int(out[1]), "q_end": int(out[2]),
+            "d_begin": int(out[3]), "d_end": int(out[4]), "ops": ops.raw[:n_ops.value].decode()}

@@ -186,3 +186,175 @@ int oracle_search(const uint8_t* query, uint32_t m, const uint8_t* db, const uin
     oracle_scores(query, m, db, offsets, NULL, n_seqs, fsbt, A, alpha, beta, scores, nthreads);
     return oracle_top_k(scores, n_seqs, top_k, top_scores, top_index, n_top);
 }
+
+/*
+ * One optimal local alignment of S1 (query, m) and S2 (database sequence, n):
+ * the traceback that Section IV.C leaves to future work. What is returned
+ * (the paper does not define it; these are the readings the tests check):
+ *
+ *  - the score S = max H[i][j] of recurrence (1);
+ *  - the end cell: the first (i, j), in order of i then j, with H[i][j] = S;
+ *    for S > 0 the alignment ends by aligning S1[i] with S2[j];
+ *  - the start cell: of the cells (i', j') from which an alignment that
+ *    begins by aligning S1[i'] with S2[j'] and ends by aligning S1[i] with
+ *    S2[j] scores S, the one with the largest i', then the largest j';
+ *  - the path: the three-state dynamic programme (M: S1[u] aligned with
+ *    S2[v]; E: S1[u] against a gap; F: S2[v] against a gap) anchored at both
+ *    cells, with the gap costs of recurrence (1) (a gap of either kind opens
+ *    from H = max(M, E, F) at cost beta and extends at cost alpha), traced
+ *    back from M at the end cell; H prefers M, then E, then F, and a gap state
+ *    prefers extending to opening when both give its value.
+ *
+ * out = {S, q_begin, q_end, d_begin, d_end} with 0-based half-open residue
+ * ranges; ops = one letter per alignment column in order: 'M' (a residue of
+ * each), 'I' (a query residue against a gap), 'D' (a database residue against
+ * a gap). S = 0 gives empty ranges and no ops. Returns 0, or -1 when ops_cap
+ * is too small or memory runs out.
+ */
+#define ORACLE_NEG (-(1 << 29))
+
+static int32_t max3i(int32_t a, int32_t b, int32_t c) { return max2(a, max2(b, c)); }
+
+int oracle_sw_align(const uint8_t* S1, uint32_t m, const uint8_t* S2, uint32_t n,
+                    const int8_t* fsbt, uint32_t A, int32_t alpha, int32_t beta, int32_t* out,
+                    char* ops, uint32_t ops_cap, uint32_t* ops_len) {
+    out[0] = out[1] = out[2] = out[3] = out[4] = 0;
+    *ops_len = 0;
+    if (m == 0 || n == 0) return 0;
+    /* 1. score and end cell: recurrence (1) row by row, the first strict maximum */
+    int32_t* H = (int32_t*)calloc((size_t)n + 1, sizeof(int32_t));
+    int32_t* E = (int32_t*)calloc((size_t)n + 1, sizeof(int32_t));
+    if (!H || !E) { free(H); free(E); return -1; }
+    int32_t S = 0;
+    uint32_t ie = 0, je = 0;
+    for (uint32_t i = 1; i <= m; ++i) {
+        int32_t diag = 0, Hleft = 0, F = 0;
+        for (uint32_t j = 1; j <= n; ++j) {
+            const int32_t e = max2(E[j] - alpha, H[j] - beta);
+            F = max2(F - alpha, Hleft - beta);
+            int32_t h = diag + fsbt[(uint32_t)S1[i - 1] * A + S2[j - 1]];
+            h = max2(max2(h, 0), max2(e, F));
+            diag = H[j];
+            H[j] = h;
+            E[j] = e;
+            Hleft = h;
+            if (h > S) { S = h; ie = i; je = j; }
+        }
+    }
+    free(H);
+    free(E);
+    if (S == 0) return 0;
+
+    /* 2. start cell: the same gap model run backwards from the end cell, anchored
+     * there; Mr[i][j] is the best score of an alignment that begins by aligning
+     * S1[i] with S2[j] and ends at the end cell (i <= ie, j <= je) */
+    const uint32_t a0 = ie, b0 = je;  /* reversed extents */
+    int32_t* Mr = (int32_t*)malloc(((size_t)a0 + 1) * (b0 + 1) * sizeof(int32_t));
+    int32_t* Er = (int32_t*)malloc(((size_t)a0 + 1) * (b0 + 1) * sizeof(int32_t));
+    int32_t* Fr = (int32_t*)malloc(((size_t)a0 + 1) * (b0 + 1) * sizeof(int32_t));
+    if (!Mr || !Er || !Fr) { free(Mr); free(Er); free(Fr); return -1; }
+#define R_(X, u, v) X[(size_t)(u) * (b0 + 1) + (v)]
+    /* reversed coordinates u = ie - i + 1, v = je - j + 1 (1-based) */
+    uint32_t is = 0, js = 0;
+    for (uint32_t u = 0; u <= a0; ++u)
+        for (uint32_t v = 0; v <= b0; ++v) {
+            if (u == 0 || v == 0) {
+                R_(Mr, u, v) = R_(Er, u, v) = R_(Fr, u, v) = ORACLE_NEG;
+                continue;
+            }
+            const uint32_t i = ie - u + 1, j = je - v + 1;
+            const int32_t s = fsbt[(uint32_t)S1[i - 1] * A + S2[j - 1]];
+            int32_t mv;
+            if (u == 1 && v == 1) mv = s;
+            else {
+                const int32_t hp = max3i(R_(Mr, u - 1, v - 1), R_(Er, u - 1, v - 1), R_(Fr, u - 1, v - 1));
+                mv = hp <= ORACLE_NEG / 2 ? ORACLE_NEG : hp + s;
+            }
+            const int32_t hu = max3i(R_(Mr, u - 1, v), R_(Er, u - 1, v), R_(Fr, u - 1, v));
+            const int32_t ev = max2(R_(Er, u - 1, v) - alpha, hu - beta);
+            const int32_t hv = max3i(R_(Mr, u, v - 1), R_(Er, u, v - 1), R_(Fr, u, v - 1));
+            const int32_t fv = max2(R_(Fr, u, v - 1) - alpha, hv - beta);
+            R_(Mr, u, v) = mv;
+            R_(Er, u, v) = ev <= ORACLE_NEG / 2 ? ORACLE_NEG : ev;
+            R_(Fr, u, v) = fv <= ORACLE_NEG / 2 ? ORACLE_NEG : fv;
+            if (mv == S && is == 0) { is = i; js = j; }  /* first in (u, v) order */
+        }
+    free(Mr);
+    free(Er);
+    free(Fr);
+#undef R_
+    if (is == 0) return -1; /* cannot happen: the alignment found in step 1 starts somewhere */
+
+    /* 3. the path: anchored three-state programme over the box, full matrices */
+    const uint32_t a = ie - is + 1, b = je - js + 1;
+    int32_t* M3 = (int32_t*)malloc(((size_t)a + 1) * (b + 1) * sizeof(int32_t));
+    int32_t* E3 = (int32_t*)malloc(((size_t)a + 1) * (b + 1) * sizeof(int32_t));
+    int32_t* F3 = (int32_t*)malloc(((size_t)a + 1) * (b + 1) * sizeof(int32_t));
+    if (!M3 || !E3 || !F3) { free(M3); free(E3); free(F3); return -1; }
+#define B_(X, u, v) X[(size_t)(u) * (b + 1) + (v)]
+    for (uint32_t u = 0; u <= a; ++u)
+        for (uint32_t v = 0; v <= b; ++v) {
+            if (u == 0 || v == 0) {
+                B_(M3, u, v) = B_(E3, u, v) = B_(F3, u, v) = ORACLE_NEG;
+                continue;
+            }
+            const int32_t s = fsbt[(uint32_t)S1[is + u - 2] * A + S2[js + v - 2]];
+            int32_t mv;
+            if (u == 1 && v == 1) mv = s;
+            else {
+                const int32_t hp = max3i(B_(M3, u - 1, v - 1), B_(E3, u - 1, v - 1), B_(F3, u - 1, v - 1));
+                mv = hp <= ORACLE_NEG / 2 ? ORACLE_NEG : hp + s;
+            }
+            const int32_t hu = max3i(B_(M3, u - 1, v), B_(E3, u - 1, v), B_(F3, u - 1, v));
+            const int32_t ev = max2(B_(E3, u - 1, v) - alpha, hu - beta);
+            const int32_t hv = max3i(B_(M3, u, v - 1), B_(E3, u, v - 1), B_(F3, u, v - 1));
+            const int32_t fv = max2(B_(F3, u, v - 1) - alpha, hv - beta);
+            B_(M3, u, v) = mv;
+            B_(E3, u, v) = ev <= ORACLE_NEG / 2 ? ORACLE_NEG : ev;
+            B_(F3, u, v) = fv <= ORACLE_NEG / 2 ? ORACLE_NEG : fv;
+        }
+    int rc = 0;
+    if (B_(M3, a, b) != S) rc = -1;
+    /* trace back from M at (a, b); letters come out reversed */
+    uint32_t u = a, v = b, len = 0;
+    int state = 0; /* 0 = M, 1 = E, 2 = F */
+    while (rc == 0) {
+        if (len >= ops_cap) { rc = -1; break; }
+        if (state == 0) {
+            ops[len++] = 'M';
+            if (u == 1 && v == 1) break;
+            --u;
+            --v;
+        } else if (state == 1) {
+            ops[len++] = 'I';
+            const int extend = B_(E3, u, v) == B_(E3, u - 1, v) - alpha;
+            --u;
+            if (extend) continue;
+        } else {
+            ops[len++] = 'D';
+            const int extend = B_(F3, u, v) == B_(F3, u, v - 1) - alpha;
+            --v;
+            if (extend) continue;
+        }
+        /* entering H at (u, v): M, then E, then F */
+        const int32_t hm = B_(M3, u, v), he = B_(E3, u, v), hf = B_(F3, u, v);
+        state = (hm >= he && hm >= hf) ? 0 : (he >= hf ? 1 : 2);
+    }
+    free(M3);
+    free(E3);
+    free(F3);
+#undef B_
+    if (rc != 0) return rc;
+    for (uint32_t k = 0; k < len / 2; ++k) {
+        const char c = ops[k];
+        ops[k] = ops[len - 1 - k];
+        ops[len - 1 - k] = c;
+    }
+    *ops_len = len;
+    out[0] = S;
+    out[1] = (int32_t)(is - 1);
+    out[2] = (int32_t)ie;
+    out[3] = (int32_t)(js - 1);
+    out[4] = (int32_t)je;
+    return 0;
+}

@@ -120,3 +120,49 @@ def ranked_top_k(scores, k):
     order = np.lexsort((np.arange(s.size), -s))
     kk = min(k, s.size)
     return s[order[:kk]].astype(np.int32), order[:kk].astype(np.uint64)
+
+
+def score_of_ops(q, d, M, alpha, beta, q_begin, d_begin, ops) -> int:
+    """Score of one alignment under recurrence (1)'s move set: 'M' adds fsbt, a gap step
+    costs beta when it opens a run and min(alpha, beta) when it continues a run of the
+    same kind ('I': a query residue against a gap, 'D': a database residue)."""
+    i, j, s, prev = q_begin, d_begin, 0, ""
+    for op in ops:
+        if op == "M":
+            s += _sub(M, q[i], d[j])
+            i += 1
+            j += 1
+        elif op == "I":
+            s -= min(alpha, beta) if prev == "I" else beta
+            i += 1
+        else:
+            s -= min(alpha, beta) if prev == "D" else beta
+            j += 1
+        prev = op
+    return s
+
+
+def brute_force_optimal_alignments(q, d, M, alpha, beta):
+    """(best score, every optimal alignment as (q_begin, q_end, d_begin, d_end, ops)) over
+    all local alignments that begin and end with an aligned pair, enumerated path by path
+    with recurrence (1)'s move set (0-based half-open ranges)."""
+    m, n = len(q), len(d)
+    found = []
+
+    def walk(i0, j0, i, j, ops, last, score):
+        if last == "M":
+            found.append((score, i0, i, j0, j, ops))
+        if i < m and j < n:
+            walk(i0, j0, i + 1, j + 1, ops + "M", "M", score + _sub(M, q[i], d[j]))
+        if i < m:
+            walk(i0, j0, i + 1, j, ops + "I", "I",
+                 score - (min(alpha, beta) if last == "I" else beta))
+        if j < n:
+            walk(i0, j0, i, j + 1, ops + "D", "D",
+                 score - (min(alpha, beta) if last == "D" else beta))
+
+    for i0 in range(m):
+        for j0 in range(n):
+            walk(i0, j0, i0 + 1, j0 + 1, "M", "M", _sub(M, q[i0], d[j0]))
+    best = max([0] + [f[0] for f in found])
+    return best, [f[1:] for f in found if f[0] == best and best > 0]
