@@ -335,6 +335,51 @@ sw_status sw_search_noalloc(const uint8_t* d_query, uint32_t qlen, const int8_t*
                             const uint8_t* d_residues, const uint64_t* d_offsets, uint32_t n_seqs,
                             uint32_t max_len, int32_t* d_scores, void* stream);
 
+/*
+ * Traceback: one optimal local alignment of the query with each listed
+ * database sequence (HOST buffers; the paper computes scores only and leaves
+ * alignments to future work, Section IV.C). For each sequence:
+ *
+ *   score        the Smith-Waterman score of recurrence (1) (as sw_search);
+ *   end cell     the first (query position, database position), in order of
+ *                query then database position, where H reaches the score; the
+ *                alignment ends by aligning those two residues;
+ *   start cell   of the optimal alignments ending there, the latest start
+ *                (largest query position, then largest database position);
+ *   path         the three-state programme anchored at both cells, traced
+ *                back from the end; H prefers an aligned pair, then a query
+ *                residue against a gap, then a database residue against a gap,
+ *                and a gap prefers extending to opening when both give its
+ *                value. These rules make the alignment unique.
+ *
+ *   db_index   : HOST, n original database indices (any order, repeats allowed)
+ *   out        : HOST, n records; ranges are 0-based and half-open; score 0
+ *                gives empty ranges and no letters
+ *   ops        : HOST, ops_cap chars; record k's letters are
+ *                ops[out[k].ops_offset .. + out[k].ops_len): 'M' aligns a
+ *                query residue with a database residue, 'I' is a query residue
+ *                against a gap, 'D' a database residue against a gap
+ *   ops_used   : HOST, receives the letters needed (also when ops_cap is too
+ *                small, which fails with SW_ERR_INVALID_ARG and fills nothing
+ *                else)
+ *
+ * Scores are computed in int32 whatever the penalties. Device memory: the box
+ * between the start and end cells takes one byte per cell (batched within
+ * 1 GiB; a larger single box takes its own size).
+ */
+typedef struct {
+    int32_t score;
+    uint32_t q_begin, q_end;    /* query residues [q_begin, q_end) */
+    uint64_t db_index;          /* database sequence (original index) */
+    uint32_t d_begin, d_end;    /* its residues [d_begin, d_end) */
+    uint64_t ops_offset;        /* first letter of this alignment in ops */
+    uint32_t ops_len;
+} sw_alignment;
+
+sw_status sw_align(sw_db* db, const uint8_t* query, uint32_t qlen, const int8_t* matrix,
+                   int32_t alpha, int32_t beta, const uint64_t* db_index, uint32_t n,
+                   sw_alignment* out, char* ops, uint64_t ops_cap, uint64_t* ops_used);
+
 /* Message for the last non-OK status returned to this thread ("" if none). */
 const char* sw_last_error(void);
 

@@ -86,6 +86,13 @@ class sw_server_stats(ctypes.Structure):
                 ("slices", ctypes.c_uint32)]
 
 
+class sw_alignment(ctypes.Structure):
+    _fields_ = [("score", ctypes.c_int32), ("q_begin", ctypes.c_uint32), ("q_end", ctypes.c_uint32),
+                ("db_index", ctypes.c_uint64), ("d_begin", ctypes.c_uint32),
+                ("d_end", ctypes.c_uint32), ("ops_offset", ctypes.c_uint64),
+                ("ops_len", ctypes.c_uint32)]
+
+
 class sw_tuning(ctypes.Structure):
     _fields_ = [("ns_per_row_residue", (ctypes.c_double * 5) * 4),
                 ("fastest_R", ctypes.c_uint32 * 4), ("int32_over_int16", ctypes.c_double),
@@ -116,6 +123,7 @@ SIGNATURES = {
     "sw_db_autotune": (ctypes.c_int, [_P, _P, _I32, _I32, ctypes.c_char_p, _P]),
     "sw_db_get_profile": (ctypes.c_int, [_P, _P]),
     "sw_db_reset_profile": (ctypes.c_int, [_P]),
+    "sw_align": (ctypes.c_int, [_P, _P, _U32, _P, _I32, _I32, _P, _U32, _P, _P, _U64, _P]),
     "sw_last_error": (ctypes.c_char_p, []),
     "sw_version": (ctypes.c_char_p, []),
 }
@@ -419,3 +427,26 @@ def sw_last_error() -> str:
 
 def sw_version() -> str:
     return load_library().sw_version().decode()
+
+
+def sw_align(db: Database, query, matrix, alpha: int, beta: int, db_index):
+    """One optimal local alignment per listed database sequence (host buffers): a list of
+    dicts with score, 0-based half-open query / database ranges and the op string."""
+    q = np.ascontiguousarray(query, dtype=np.uint8)
+    m = np.ascontiguousarray(matrix, dtype=np.int8)
+    idx = np.ascontiguousarray(db_index, dtype=np.uint64)
+    n = int(idx.size)
+    out = (sw_alignment * max(n, 1))()
+    used = ctypes.c_uint64(0)
+    cap = max(1, n * (int(q.size) + int(db.info()["max_length"])))  # an alignment has at most
+    ops = ctypes.create_string_buffer(cap)                          # |query| + |sequence| letters
+    _check(load_library().sw_align(db.handle, _ptr(q), q.size, _ptr(m), int(alpha), int(beta),
+                                   _ptr(idx), n, out, ops, cap, ctypes.byref(used)))
+    raw = ops.raw
+    res = []
+    for k in range(n):
+        o = out[k]
+        res.append({"score": o.score, "q_begin": o.q_begin, "q_end": o.q_end,
+                    "db_index": o.db_index, "d_begin": o.d_begin, "d_end": o.d_end,
+                    "ops": raw[o.ops_offset:o.ops_offset + o.ops_len].decode()})
+    return res

@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 LIB_NAME = "libswgb300.so"
 
 SOURCES = ["sw_wavefront.cu", "sw_rescore.cu", "sw_topk.cu", "sw_api.cu", "sw_search.cu",
-           "sw_noalloc.cu", "sw_server.cu", "sw_tune.cu"]
+           "sw_noalloc.cu", "sw_server.cu", "sw_tune.cu", "sw_align.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr"]

@@ -1,0 +1,472 @@
+// Traceback: one optimal local alignment per requested database sequence.
+//
+// Section IV.C leaves the alignments themselves (not only their scores) to
+// future work; a database search reports them for its top hits. Three
+// dynamic programmes per (query, sequence) pair, in int32, each a lane
+// wavefront of one warp (lane t on column s - t at step s, kR query rows per
+// lane, passes of 256 rows with the bottom row kept in the warp's scratch):
+//
+//  1. recurrence (1) with the score S and the end cell: the first (i, j), in
+//     order of i then j, whose H equals S;
+//  2. the same gap model run backwards from the end cell and anchored there
+//     (no zero floor): the start cell is the first cell in that reversed order
+//     whose aligned-pair value equals S, i.e. the latest start of an optimal
+//     alignment ending at the end cell;
+//  3. the three-state programme (M: a pair aligned, E: a query residue
+//     against a gap, F: a database residue against a gap) over the box between
+//     the two cells, anchored at both, writing for every cell which state
+//     gives H (M, then E, then F on ties) and whether E and F extend (extension
+//     preferred on ties) as one byte; lane 0 then walks the bytes back from M
+//     at the end cell and writes the op string.
+//
+// The end and start cells and the tie rules make the alignment unique, so it
+// can be compared letter for letter.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+#include "sw.h"
+#include "sw_db.h"
+#include "sw_internal.h"
+
+namespace swgb {
+
+namespace {
+
+constexpr int kWarps = 8;
+constexpr int kThreads = kWarps * 32;
+constexpr int kT = 32;
+constexpr int kR = 8;
+constexpr int kRows = kT * kR;
+constexpr int kM = kProfileRows;
+constexpr int32_t kNeg = -(1 << 29);  // minus infinity for the anchored programmes
+
+struct AlignHit {
+    uint64_t sp;        // sorted position of the sequence
+    uint32_t n;         // its length
+    uint32_t pad0;
+    int32_t score;      // phase 0 outputs
+    uint32_t ie, je, is, js;
+    uint32_t ops_len;   // phase 1 output (0xffffffff: inconsistent bytes, see below)
+    uint64_t dir_off;   // phase 1 inputs: offsets of its box bytes and of its ops
+    uint64_t ops_off;
+};
+
+struct AlignArgs {
+    const uint8_t* tile_data;
+    const uint64_t* tile_off;
+    const uint8_t* query;
+    uint32_t qlen;
+    const int8_t* matrix;
+    uint32_t alphabet;
+    int32_t alpha, beta;
+    AlignHit* hits;
+    uint32_t first, count;
+    uint2* boundary;    // per warp: two halves of bstride / 2 entries
+    uint64_t bstride;
+    uint8_t* dir;
+    char* ops;
+    int phase;          // 0: score, end and start cells; 1: box programme and traceback
+};
+
+__device__ __forceinline__ int32_t imax(int32_t a, int32_t b) { return a > b ? a : b; }
+
+// One dynamic programme over rows x cols by one warp. MODE 0: recurrence (1),
+// tracking the first maximal cell; MODE 1: anchored at (0, 0), tracking the first
+// cell whose aligned-pair value is S; MODE 2: anchored at (0, 0), writing each
+// cell's traceback byte to dir[row * cols + col].
+template <int MODE, class QF, class DF>
+__device__ void run_dp(const AlignArgs& a, const int32_t* sM, uint2* bnd0, uint64_t half, int t,
+                       uint32_t rows, uint32_t cols, QF qf, DF df, int32_t S, int32_t& best,
+                       uint32_t& bi, uint32_t& bj, uint8_t* dir) {
+    const int32_t border = MODE == 0 ? 0 : kNeg;
+    const uint32_t P = (rows + kRows - 1) / kRows;
+    const uint32_t steps = cols + kT - 1;
+    for (uint32_t p = 0; p < P; ++p) {
+        uint32_t qc[kR];
+#pragma unroll
+        for (int r = 0; r < kR; ++r) {
+            const uint32_t row = p * kRows + (uint32_t)t * kR + r;
+            uint32_t c = row < rows ? qf(row) : kPadCode;
+            qc[r] = (c < a.alphabet ? c : kPadCode) * kM;
+        }
+        int32_t Hl[kR], Fr[kR];
+        uint32_t fx = 0;  // MODE 2: extension bit of Fr[r] in bit r
+#pragma unroll
+        for (int r = 0; r < kR; ++r) { Hl[r] = border; Fr[r] = border; }
+        int32_t hb_out = border, eb_out = border, hdiag0 = border;
+        uint32_t code_out = kPadCode, ex_out = 0;
+        const uint2* bin = bnd0 + (p & 1) * half + kT;
+        uint2* bout = bnd0 + ((p + 1) & 1) * half + kT;
+        for (uint32_t s = 0; s < steps; ++s) {
+            int32_t h_in = (int32_t)__shfl_up_sync(0xffffffffu, (uint32_t)hb_out, 1);
+            int32_t e_in = (int32_t)__shfl_up_sync(0xffffffffu, (uint32_t)eb_out, 1);
+            uint32_t code = __shfl_up_sync(0xffffffffu, code_out, 1);
+            uint32_t ex = __shfl_up_sync(0xffffffffu, ex_out, 1);
+            if (t == 0) {
+                code = s < cols ? df(s) : kPadCode;
+                if (code > kPadCode) code = kPadCode;
+                h_in = border;
+                e_in = border;
+                ex = 0;
+                if (p > 0 && s < cols) {
+                    const uint2 v = bin[s];
+                    h_in = (int32_t)v.x;
+                    e_in = MODE == 2 ? ((int32_t)v.y >> 1) : (int32_t)v.y;
+                    ex = MODE == 2 ? (v.y & 1u) : 0u;
+                }
+            }
+            code_out = code;
+            const int64_t j = (int64_t)s - t;
+            int32_t diag = hdiag0, E = e_in;
+#pragma unroll
+            for (int r = 0; r < kR; ++r) {
+                const uint32_t i = p * kRows + (uint32_t)t * kR + r;
+                const bool valid = i < rows && j >= 0 && j < (int64_t)cols;
+                const int32_t sc = sM[qc[r] + code];
+                int32_t H, En, Fn;
+                if (MODE == 0) {
+                    H = imax(imax(diag + sc, 0), imax(E, Fr[r]));
+                    if (valid && (H > best || (H == best && (i < bi || (i == bi && (uint32_t)j < bj))))) {
+                        best = H;
+                        bi = i;
+                        bj = (uint32_t)j;
+                    }
+                    const int32_t hb = H - a.beta;
+                    En = imax(E - a.alpha, hb);
+                    Fn = imax(Fr[r] - a.alpha, hb);
+                } else {
+                    const int32_t Mv = (i == 0 && j == 0) ? sc : imax(diag + sc, kNeg);
+                    const int32_t F = Fr[r];
+                    H = imax(Mv, imax(E, F));
+                    if (MODE == 1) {
+                        if (valid && Mv == S && (i < bi || (i == bi && (uint32_t)j < bj))) {
+                            bi = i;
+                            bj = (uint32_t)j;
+                        }
+                    } else if (valid) {
+                        const uint32_t hsel = (Mv >= E && Mv >= F) ? 0u : (E >= F ? 1u : 2u);
+                        dir[(uint64_t)i * cols + (uint64_t)j] =
+                            (uint8_t)(hsel | (ex << 2) | (((fx >> r) & 1u) << 3));
+                    }
+                    const int32_t hb = H - a.beta;
+                    const uint32_t exn = (E - a.alpha >= hb) ? 1u : 0u;
+                    const uint32_t fxn = (F - a.alpha >= hb) ? 1u : 0u;
+                    En = imax(imax(E - a.alpha, hb), kNeg);
+                    Fn = imax(imax(F - a.alpha, hb), kNeg);
+                    if (!valid) {
+                        H = kNeg;
+                        En = kNeg;
+                        Fn = kNeg;
+                    }
+                    ex = valid ? exn : 0u;
+                    if (MODE == 2) fx = (fx & ~(1u << r)) | ((valid ? fxn : 0u) << r);
+                }
+                diag = Hl[r];
+                Hl[r] = H;
+                E = En;
+                Fr[r] = Fn;
+            }
+            hb_out = Hl[kR - 1];
+            eb_out = E;
+            ex_out = ex;
+            hdiag0 = h_in;
+            if (t == kT - 1 && p + 1 < P && j >= 0 && j < (int64_t)cols) {
+                const uint32_t ev = MODE == 2 ? ((uint32_t)eb_out << 1) | ex_out : (uint32_t)eb_out;
+                bout[j] = make_uint2((uint32_t)hb_out, ev);
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) align_kernel(const AlignArgs a) {
+    __shared__ int32_t sM[kM * kM];
+    for (uint32_t i = threadIdx.x; i < kM * kM; i += kThreads) {
+        const uint32_t r = i / kM, c = i % kM;
+        sM[i] = (r < a.alphabet && c < a.alphabet) ? (int32_t)a.matrix[r * a.alphabet + c] : 0;
+    }
+    __syncthreads();
+    const int w = threadIdx.x >> 5, t = threadIdx.x & 31;
+    const uint64_t slot = (uint64_t)blockIdx.x * kWarps + w;
+    const uint64_t nwarps = (uint64_t)gridDim.x * kWarps;
+    uint2* const bnd0 = a.boundary + slot * a.bstride;
+    const uint64_t half = a.bstride / 2;
+    const uint8_t* q = a.query;
+
+    for (uint64_t h = a.first + slot; h < (uint64_t)a.first + a.count; h += nwarps) {
+        AlignHit& hit = a.hits[h];
+        const uint64_t sp = hit.sp;
+        const uint8_t* seq = a.tile_data + a.tile_off[sp / kTileSeqs] +
+                             ((sp >> 1) & (kTilePairs - 1)) * 8 + (sp & 1);
+        auto dcode = [seq](uint32_t j) -> uint32_t { return seq[(size_t)(j >> 2) * 32 + (j & 3) * 2]; };
+        const uint32_t n = hit.n;
+        if (a.phase == 0) {
+            int32_t best = 0;
+            uint32_t bi = 0xffffffffu, bj = 0xffffffffu;
+            if (a.qlen && n)
+                run_dp<0>(a, sM, bnd0, half, t, a.qlen, n, [q](uint32_t i) -> uint32_t { return q[i]; },
+                          dcode, 0, best, bi, bj, nullptr);
+            // first maximal cell over the warp
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const int32_t ob = (int32_t)__shfl_xor_sync(0xffffffffu, (uint32_t)best, o);
+                const uint32_t oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                const uint32_t oj = __shfl_xor_sync(0xffffffffu, bj, o);
+                if (ob > best || (ob == best && (oi < bi || (oi == bi && oj < bj)))) {
+                    best = ob;
+                    bi = oi;
+                    bj = oj;
+                }
+            }
+            uint32_t is = 0, js = 0;
+            if (best > 0) {
+                const uint32_t ie = bi, je = bj;
+                int32_t unused = 0;
+                uint32_t ui = 0xffffffffu, uj = 0xffffffffu;
+                run_dp<1>(a, sM, bnd0, half, t, ie + 1, je + 1,
+                          [q, ie](uint32_t u) -> uint32_t { return q[ie - u]; },
+                          [dcode, je](uint32_t v) -> uint32_t { return dcode(je - v); }, best, unused,
+                          ui, uj, nullptr);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const uint32_t oi = __shfl_xor_sync(0xffffffffu, ui, o);
+                    const uint32_t oj = __shfl_xor_sync(0xffffffffu, uj, o);
+                    if (oi < ui || (oi == ui && oj < uj)) {
+                        ui = oi;
+                        uj = oj;
+                    }
+                }
+                // ui is always found (the optimal alignment starts somewhere); guard anyway
+                is = ui <= ie ? ie - ui : 0;
+                js = uj <= je ? je - uj : 0;
+            }
+            if (t == 0) {
+                hit.score = best;
+                hit.ie = best > 0 ? bi : 0;
+                hit.je = best > 0 ? bj : 0;
+                hit.is = is;
+                hit.js = js;
+            }
+        } else {
+            if (hit.score <= 0) {
+                if (t == 0) hit.ops_len = 0;
+                continue;
+            }
+            const uint32_t is = hit.is, js = hit.js;
+            const uint32_t rows = hit.ie - is + 1, cols = hit.je - js + 1;
+            uint8_t* dir = a.dir + hit.dir_off;
+            int32_t unused = 0;
+            uint32_t ui = 0, uj = 0;
+            run_dp<2>(a, sM, bnd0, half, t, rows, cols,
+                      [q, is](uint32_t u) -> uint32_t { return q[is + u]; },
+                      [dcode, js](uint32_t v) -> uint32_t { return dcode(js + v); }, hit.score,
+                      unused, ui, uj, dir);
+            __syncwarp();
+            if (t == 0) {
+                // walk back from M at the end cell; letters come out reversed
+                char* out = a.ops + hit.ops_off;
+                const uint32_t cap = rows + cols;
+                uint32_t u = rows - 1, v = cols - 1, len = 0, state = 0;
+                bool ok = true;
+                for (;;) {
+                    if (len >= cap) { ok = false; break; }
+                    const uint8_t b = dir[(uint64_t)u * cols + v];
+                    if (state == 0) {
+                        out[len++] = 'M';
+                        if (u == 0 && v == 0) break;
+                        if (u == 0 || v == 0) { ok = false; break; }
+                        --u;
+                        --v;
+                        state = dir[(uint64_t)u * cols + v] & 3u;
+                    } else if (state == 1) {
+                        out[len++] = 'I';
+                        if (u == 0) { ok = false; break; }
+                        --u;
+                        state = ((b >> 2) & 1u) ? 1u : (dir[(uint64_t)u * cols + v] & 3u);
+                    } else {
+                        out[len++] = 'D';
+                        if (v == 0) { ok = false; break; }
+                        --v;
+                        state = ((b >> 3) & 1u) ? 2u : (dir[(uint64_t)u * cols + v] & 3u);
+                    }
+                    if (state > 2) { ok = false; break; }
+                }
+                if (ok) {
+                    for (uint32_t k = 0; k < len / 2; ++k) {
+                        const char c = out[k];
+                        out[k] = out[len - 1 - k];
+                        out[len - 1 - k] = c;
+                    }
+                }
+                hit.ops_len = ok ? len : 0xffffffffu;
+            }
+        }
+    }
+}
+
+}  // namespace
+
+}  // namespace swgb
+
+using namespace swgb;
+
+extern "C" sw_status sw_align(sw_db* db, const uint8_t* query, uint32_t qlen, const int8_t* matrix,
+                              int32_t alpha, int32_t beta, const uint64_t* db_index, uint32_t n,
+                              sw_alignment* out, char* ops, uint64_t ops_cap, uint64_t* ops_used) {
+    clear_error();
+    sw_status st;
+    if ((st = check_common(db, qlen, alpha, beta, 0, "sw_align"))) return st;
+    if ((st = validate_host_query(db, query, qlen, matrix, "sw_align"))) return st;
+    if (n && (!db_index || !out)) return fail(SW_ERR_INVALID_ARG, "sw_align: NULL db_index or out");
+    if (!ops_used) return fail(SW_ERR_INVALID_ARG, "sw_align: NULL ops_used");
+    *ops_used = 0;
+    if (n == 0) return SW_OK;
+    std::vector<AlignHit> hits(n);
+    for (uint32_t k = 0; k < n; ++k) {
+        if (db_index[k] >= db->n_seqs)
+            return fail(SW_ERR_INVALID_ARG, "sw_align: db_index %llu out of range",
+                        (unsigned long long)db_index[k]);
+        std::memset(&hits[k], 0, sizeof(AlignHit));
+        hits[k].sp = db->pos_of[db_index[k]];
+        hits[k].n = db->seq_len[db_index[k]];
+    }
+    DeviceScope scope(db->device);
+    if ((st = stage_query(db, query, qlen, matrix))) return st;
+
+    // scratch: per-warp boundary rows, the hits, and (per batch) box bytes and ops
+    const uint64_t bstride = 2ull * (((uint64_t)std::max(db->max_len, qlen) + kT + 8 + 3) & ~3ull);
+    const uint64_t warp_bytes = bstride * sizeof(uint2);
+    const int grid = (int)std::max<uint64_t>(
+        1, std::min<uint64_t>({(uint64_t)db->nsm * 2, (n + kWarps - 1) / kWarps,
+                               (256ull << 20) / (warp_bytes * kWarps) + 1}));
+    void* d_bnd = nullptr;
+    AlignHit* d_hits = nullptr;
+    cudaError_t e;
+    if ((e = db_malloc(db, &d_bnd, (size_t)grid * kWarps * warp_bytes)) != cudaSuccess)
+        return cuda_fail(e, "sw_align: scratch rows");
+    if ((e = db_malloc(db, (void**)&d_hits, n * sizeof(AlignHit))) != cudaSuccess) {
+        db_free(db, d_bnd, (size_t)grid * kWarps * warp_bytes);
+        return cuda_fail(e, "sw_align: hit table");
+    }
+    auto cleanup = [&](void* dir, size_t dir_bytes, void* dops, size_t ops_bytes) {
+        if (dir) db_free(db, dir, dir_bytes);
+        if (dops) db_free(db, dops, ops_bytes);
+        db_free(db, d_hits, n * sizeof(AlignHit));
+        db_free(db, d_bnd, (size_t)grid * kWarps * warp_bytes);
+    };
+    AlignArgs a{};
+    a.tile_data = db->d_tile_data;
+    a.tile_off = db->d_tile_off;
+    a.query = db->d_query;
+    a.qlen = qlen;
+    a.matrix = db->d_matrix;
+    a.alphabet = db->alphabet;
+    a.alpha = alpha;
+    a.beta = beta;
+    a.hits = d_hits;
+    a.boundary = (uint2*)d_bnd;
+    a.bstride = bstride;
+    // phase 0: scores, end and start cells of every hit
+    if ((e = cudaMemcpyAsync(d_hits, hits.data(), n * sizeof(AlignHit), cudaMemcpyHostToDevice,
+                             db->stream)) != cudaSuccess) {
+        cleanup(nullptr, 0, nullptr, 0);
+        return cuda_fail(e, "sw_align: upload");
+    }
+    a.first = 0;
+    a.count = n;
+    a.phase = 0;
+    align_kernel<<<grid, kThreads, 0, db->stream>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess ||
+        (e = cudaMemcpyAsync(hits.data(), d_hits, n * sizeof(AlignHit), cudaMemcpyDeviceToHost,
+                             db->stream)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(db->stream)) != cudaSuccess) {
+        cleanup(nullptr, 0, nullptr, 0);
+        return cuda_fail(e, "sw_align: score and end cells");
+    }
+    // phase 1 in batches whose box bytes fit the budget
+    const uint64_t kDirBudget = 1ull << 30;
+    uint64_t max_box = 0;
+    for (auto& h : hits)
+        if (h.score > 0)
+            max_box = std::max<uint64_t>(max_box, (uint64_t)(h.ie - h.is + 1) * (h.je - h.js + 1));
+    const uint64_t dir_cap = std::max<uint64_t>(std::max<uint64_t>(max_box, kDirBudget), 256);
+    uint64_t ops_cap_dev = 0;
+    for (auto& h : hits)
+        if (h.score > 0) ops_cap_dev += (uint64_t)(h.ie - h.is + 1) + (h.je - h.js + 1);
+    ops_cap_dev = std::max<uint64_t>(ops_cap_dev, 256);
+    void* d_dir = nullptr;
+    char* d_ops = nullptr;
+    if ((e = db_malloc(db, &d_dir, dir_cap)) != cudaSuccess) {
+        cleanup(nullptr, 0, nullptr, 0);
+        return cuda_fail(e, "sw_align: traceback bytes");
+    }
+    if ((e = db_malloc(db, (void**)&d_ops, ops_cap_dev)) != cudaSuccess) {
+        cleanup(d_dir, dir_cap, nullptr, 0);
+        return cuda_fail(e, "sw_align: op strings");
+    }
+    uint64_t ops_off = 0;
+    for (auto& h : hits) {
+        h.ops_off = ops_off;
+        if (h.score > 0) ops_off += (uint64_t)(h.ie - h.is + 1) + (h.je - h.js + 1);
+    }
+    for (uint32_t b0 = 0; b0 < n;) {
+        uint64_t used = 0;
+        uint32_t b1 = b0;
+        for (; b1 < n; ++b1) {
+            const AlignHit& h = hits[b1];
+            const uint64_t box = h.score > 0 ? (uint64_t)(h.ie - h.is + 1) * (h.je - h.js + 1) : 0;
+            if (b1 > b0 && used + box > dir_cap) break;
+            hits[b1].dir_off = used;
+            used += (box + 15) & ~15ull;
+        }
+        if ((e = cudaMemcpyAsync(d_hits + b0, hits.data() + b0, (b1 - b0) * sizeof(AlignHit),
+                                 cudaMemcpyHostToDevice, db->stream)) != cudaSuccess)
+            break;
+        a.first = b0;
+        a.count = b1 - b0;
+        a.phase = 1;
+        a.dir = (uint8_t*)d_dir;
+        a.ops = d_ops;
+        align_kernel<<<grid, kThreads, 0, db->stream>>>(a);
+        if ((e = cudaGetLastError()) != cudaSuccess) break;
+        b0 = b1;
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(hits.data(), d_hits, n * sizeof(AlignHit), cudaMemcpyDeviceToHost,
+                            db->stream);
+    std::vector<char> host_ops(ops_off);
+    if (e == cudaSuccess && ops_off)
+        e = cudaMemcpyAsync(host_ops.data(), d_ops, ops_off, cudaMemcpyDeviceToHost, db->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(db->stream);
+    cleanup(d_dir, dir_cap, d_ops, ops_cap_dev);
+    if (e != cudaSuccess) return cuda_fail(e, "sw_align: traceback");
+    uint64_t total = 0;
+    for (auto& h : hits) {
+        if (h.ops_len == 0xffffffffu)
+            return fail(SW_ERR_INTERNAL, "sw_align: traceback left its box");
+        total += h.ops_len;
+    }
+    *ops_used = total;
+    if (total > ops_cap || (total && !ops))
+        return fail(SW_ERR_INVALID_ARG, "sw_align: ops buffer holds %llu letters, %llu needed",
+                    (unsigned long long)ops_cap, (unsigned long long)total);
+    uint64_t pos = 0;
+    for (uint32_t k = 0; k < n; ++k) {
+        const AlignHit& h = hits[k];
+        sw_alignment& o = out[k];
+        o.db_index = db_index[k];
+        o.score = h.score;
+        o.q_begin = h.score > 0 ? h.is : 0;
+        o.q_end = h.score > 0 ? h.ie + 1 : 0;
+        o.d_begin = h.score > 0 ? h.js : 0;
+        o.d_end = h.score > 0 ? h.je + 1 : 0;
+        o.ops_offset = pos;
+        o.ops_len = h.ops_len;
+        if (h.ops_len) std::memcpy(ops + pos, host_ops.data() + h.ops_off, h.ops_len);
+        pos += h.ops_len;
+    }
+    return SW_OK;
+}

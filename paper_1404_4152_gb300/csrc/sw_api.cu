@@ -173,6 +173,7 @@ extern "C" sw_status sw_db_load(const uint8_t* residues, const uint64_t* offsets
     db->n_seqs = n_seqs;
     db->total_residues = total;
     db->max_len = max_len;
+    db->seq_len = len;
     db->long_threshold = (opts && opts->long_threshold) ? opts->long_threshold : 3000u;
     db->budget = opts ? opts->device_budget : 0;
     db->flags = opts ? opts->flags : 0;
@@ -204,6 +205,9 @@ extern "C" sw_status sw_db_load(const uint8_t* residues, const uint64_t* offsets
     const uint64_t n_tiles = (n_seqs + kTileSeqs - 1) / kTileSeqs;
     std::vector<uint32_t> sorted(n_tiles * kTileSeqs, 0xffffffffu);
     for (uint64_t s = 0; s < n_seqs; ++s) sorted[count[max_len - len[s]]++] = (uint32_t)s;
+    db->pos_of.assign(n_seqs, 0);
+    for (uint64_t p = 0; p < sorted.size(); ++p)
+        if (sorted[p] != 0xffffffffu) db->pos_of[sorted[p]] = (uint32_t)p;
 
     std::vector<uint64_t> tile_off(n_tiles);
     std::vector<uint32_t> tile_len(n_tiles);

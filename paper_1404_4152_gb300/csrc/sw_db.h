@@ -63,6 +63,8 @@ struct sw_db {
     uint64_t* d_tile_off = nullptr;
     uint32_t* d_tile_len = nullptr;
     uint32_t* d_sorted = nullptr;  // sorted position -> original index
+    std::vector<uint32_t> pos_of;  // host: original index -> sorted position
+    std::vector<uint32_t> seq_len; // host: sequence lengths (original order)
     int32_t* d_scores = nullptr;   // internal score row (original order)
     uint2* d_flags2 = nullptr;     // (query row, sorted position) rescored in int32
     uint32_t* d_misc = nullptr;
@@ -116,6 +118,23 @@ struct sw_db {
 };
 
 namespace swgb {
+
+// Shared by the search and alignment entry points (sw_search.cu).
+sw_status check_common(const sw_db* db, uint32_t qlen, int32_t alpha, int32_t beta,
+                       uint32_t top_k, const char* fn);
+sw_status validate_host_query(const sw_db* db, const uint8_t* query, uint32_t qlen,
+                              const int8_t* matrix, const char* fn);
+sw_status stage_query(sw_db* db, const uint8_t* query, uint32_t qlen, const int8_t* matrix);
+struct DeviceScope {
+    int prev = -1;
+    explicit DeviceScope(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        cudaSetDevice(dev);
+    }
+    ~DeviceScope() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
 
 sw_status fail(sw_status st, const char* fmt, ...);
 sw_status cuda_fail(cudaError_t e, const char* what);

@@ -540,7 +540,9 @@ sw_status enqueue_batch(sw_db* db, uint32_t nq, const uint8_t* d_queries,
 
 namespace {
 
-sw_status check_common(const sw_db* db, uint32_t qlen, int32_t alpha, int32_t beta,
+}  // namespace
+
+sw_status swgb::check_common(const sw_db* db, uint32_t qlen, int32_t alpha, int32_t beta,
                        uint32_t top_k, const char* fn) {
     if (!db) return fail(SW_ERR_INVALID_ARG, "%s: db is NULL", fn);
     if (qlen == 0) return fail(SW_ERR_INVALID_ARG, "%s: qlen must be >= 1", fn);
@@ -551,18 +553,7 @@ sw_status check_common(const sw_db* db, uint32_t qlen, int32_t alpha, int32_t be
     return SW_OK;
 }
 
-struct DeviceScope {
-    int prev = -1;
-    explicit DeviceScope(int dev) {
-        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-        cudaSetDevice(dev);
-    }
-    ~DeviceScope() {
-        if (prev >= 0) cudaSetDevice(prev);
-    }
-};
-
-sw_status stage_query(sw_db* db, const uint8_t* query, uint32_t qlen, const int8_t* matrix) {
+sw_status swgb::stage_query(sw_db* db, const uint8_t* query, uint32_t qlen, const int8_t* matrix) {
     cudaError_t e;
     if (qlen > db->query_cap) {
         void* p = nullptr;
@@ -583,7 +574,7 @@ sw_status stage_query(sw_db* db, const uint8_t* query, uint32_t qlen, const int8
     return SW_OK;
 }
 
-sw_status validate_host_query(const sw_db* db, const uint8_t* query, uint32_t qlen,
+sw_status swgb::validate_host_query(const sw_db* db, const uint8_t* query, uint32_t qlen,
                               const int8_t* matrix, const char* fn) {
     if (!query || !matrix) return fail(SW_ERR_INVALID_ARG, "%s: query or matrix is NULL", fn);
     for (uint32_t i = 0; i < qlen; ++i)
@@ -592,6 +583,8 @@ sw_status validate_host_query(const sw_db* db, const uint8_t* query, uint32_t ql
                         query[i], i, db->alphabet);
     return SW_OK;
 }
+
+namespace {
 
 sw_status check_batch(const sw_db* db, uint32_t nq, const uint64_t* qoffsets, int32_t alpha,
                       int32_t beta, uint32_t top_k, const char* fn) {

@@ -1,0 +1,88 @@
+"""GPU traceback (sw_align) vs the oracle's alignment: score, both cells and every letter."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests import pins
+
+pytestmark = pytest.mark.gpu
+
+sw = pytest.importorskip("paper_1404_4152_gb300")
+
+
+def _seq(res, off, i):
+    return res[int(off[i]):int(off[i + 1])]
+
+
+def _check(db, res, off, q, M, alpha, beta, idx):
+    got = sw.sw_align(db, q, M, alpha, beta, idx)
+    assert len(got) == len(idx)
+    for g, i in zip(got, idx):
+        d = _seq(res, off, int(i))
+        e = oracle.align(q, d, M, alpha, beta)
+        assert g["db_index"] == int(i)
+        for k in ("score", "q_begin", "q_end", "d_begin", "d_end", "ops"):
+            assert g[k] == e[k], (int(i), k, g[k] if k != "ops" else g[k][:80],
+                                  e[k] if k != "ops" else e[k][:80])
+        if g["score"]:
+            assert pins.score_of_ops(q, d, M, alpha, beta, g["q_begin"], g["d_begin"],
+                                     g["ops"]) == g["score"]
+    return got
+
+
+def test_top_hits_and_random_sequences():
+    w = synth.config0()
+    q = w.queries[0]
+    with sw.sw_db_load(w.residues, w.offsets) as db:
+        _, ts, ti, _ = sw.sw_search(db, q, w.matrix, w.alpha, w.beta, 20, want_scores=False)
+        rng = np.random.default_rng(11)
+        idx = np.concatenate([ti, rng.integers(0, w.n_seqs, size=60), ti[:3]]).astype(np.uint64)
+        got = _check(db, w.residues, w.offsets, q, w.matrix, w.alpha, w.beta, idx)
+        assert [g["score"] for g in got[:20]] == list(ts)
+
+
+@pytest.mark.parametrize("ab", [(1, 11), (2, 12), (0, 5), (5, 2), (0, 0), (3, 0)])
+def test_penalties_and_multipass(ab):
+    """Queries and sequences longer than one 256-row band and one 64-column block."""
+    alpha, beta = ab
+    q = synth.make_queries([700], 21 + alpha)[0]
+    seqs = [synth.mutate(q, 22, 10 * alpha + beta, k, 800) for k in range(6)]
+    seqs += [synth.make_queries([L], 23 + L)[0] for L in (1, 5, 300, 1500)]
+    seqs.append(np.concatenate([synth.make_queries([400], 24)[0], q[100:500],
+                                synth.make_queries([300], 25)[0]]))
+    res = np.concatenate(seqs)
+    off = np.zeros(len(seqs) + 1, np.uint64)
+    off[1:] = np.cumsum([s.size for s in seqs])
+    with sw.sw_db_load(res, off) as db:
+        _check(db, res, off, q, synth.BLOSUM62, alpha, beta, np.arange(len(seqs), dtype=np.uint64))
+
+
+@pytest.mark.parametrize("A", [4, 24, 32])
+def test_alphabets_asymmetric(A):
+    rng = np.random.default_rng(300 + A)
+    M = rng.integers(-5, 7, size=(A, A)).astype(np.int8)
+    lengths = (synth.gen_lengths(80, synth.db_qtable(), 301, 1) // 2 + 1).astype(np.uint64)
+    res = rng.integers(0, A, size=int(lengths.sum())).astype(np.uint8)
+    off = np.zeros(lengths.size + 1, np.uint64)
+    off[1:] = np.cumsum(lengths)
+    q = rng.integers(0, A, size=333).astype(np.uint8)
+    with sw.sw_db_load(res, off, alphabet=A) as db:
+        _check(db, res, off, q, M, 2, 9, np.arange(lengths.size, dtype=np.uint64))
+
+
+def test_scores_beyond_16_bits_and_edge_cases():
+    """Near-copies under 8x BLOSUM62 score above 32767 (int32 throughout); empty and
+    unrelated sequences give score 0 and no letters; repeats and an empty request."""
+    q = synth.make_queries([1200], 31)[0]
+    seqs = [synth.mutate(q, 32, 0, k, 300) for k in range(3)]
+    seqs += [np.zeros(0, np.uint8), synth.make_queries([50], 33)[0]]
+    res = np.concatenate(seqs)
+    off = np.zeros(len(seqs) + 1, np.uint64)
+    off[1:] = np.cumsum([s.size for s in seqs])
+    M = (synth.BLOSUM62.astype(np.int32) * 8).astype(np.int8)
+    with sw.sw_db_load(res, off) as db:
+        got = _check(db, res, off, q, M, 8, 88, np.array([0, 1, 2, 3, 4, 0], np.uint64))
+        assert got[0]["score"] > 32767 and got[3]["score"] == 0 and got[3]["ops"] == ""
+        assert got[5] == got[0]
+        assert sw.sw_align(db, q, M, 8, 88, np.zeros(0, np.uint64)) == []
