@@ -81,6 +81,8 @@ def parse_args():
     p.add_argument("--serve-arrivals", type=int, default=16)
     p.add_argument("--long-steps", type=int, default=2,
                    help="timed searches of the long-sequence workloads (config 4 and 4b; 0 skips)")
+    p.add_argument("--align-top", type=int, default=10,
+                   help="alignments (traceback) of this many top hits per config-1 query (0 skips)")
     p.add_argument("--no-tune", action="store_true")
     return p.parse_args()
 
@@ -278,6 +280,49 @@ def run_long(args, sw, torch, dev, rank):
                     "gpu_launches": int(prof["launches"]),
                     "planted_above_16_bit": saturated})
     return out
+
+
+def run_traceback(args, sw, w, db, top_index, qlens):
+    """Alignments of the top hits of every config-1 query through sw_align (host buffers,
+    wall clock; the second of two rounds is timed), with the dynamic-programming cells of
+    its three passes, and the oracle's traceback of a few of them on the host for scale."""
+    import oracle
+
+    k = min(args.align_top, top_index.shape[1])
+    idx = [np.ascontiguousarray(top_index[i, :k], dtype=np.uint64) for i in range(len(qlens))]
+    off = w.offsets
+    for rnd in range(2):
+        t0 = time.perf_counter()
+        res = [sw.sw_align(db, w.queries[i], w.matrix, w.alpha, w.beta, idx[i])
+               for i in range(len(qlens))]
+        secs = time.perf_counter() - t0
+    n_al = sum(len(r) for r in res)
+    cells = 0
+    for i, r in enumerate(res):
+        for a in r:
+            n = int(off[a["db_index"] + 1] - off[a["db_index"]])
+            cells += qlens[i] * n
+            if a["score"] > 0:
+                cells += a["q_end"] * a["d_end"]  # the anchored pass behind the end cell
+                cells += (a["q_end"] - a["q_begin"]) * (a["d_end"] - a["d_begin"])
+    # the oracle on the top hit of every query (one core)
+    t0 = time.perf_counter()
+    for i, r in enumerate(res):
+        a = r[0]
+        oracle.align(w.queries[i], w.residues[int(off[a["db_index"]]):int(off[a["db_index"] + 1])],
+                     w.matrix, w.alpha, w.beta)
+    cpu_secs = time.perf_counter() - t0
+    gpu_top = None  # the same 20 alignments on the GPU, one call each
+    t0 = time.perf_counter()
+    for i in range(len(qlens)):
+        sw.sw_align(db, w.queries[i], w.matrix, w.alpha, w.beta, idx[i][:1])
+    gpu_top = time.perf_counter() - t0
+    return {"workload": f"top {k} hits of each of the {len(qlens)} config-1 queries: one optimal "
+                        f"alignment each (score, end and start cells, op string)",
+            "alignments": n_al, "ms": secs * 1e3, "alignments_per_s": n_al / secs,
+            "dp_cells": cells, "gcups": cells / secs / 1e9,
+            "mean_ops_len": float(np.mean([len(a["ops"]) for r in res for a in r])),
+            "top1_per_query_ms": {"gpu": gpu_top * 1e3, "cpu_oracle_1_core": cpu_secs * 1e3}}
 
 
 def run_served(args, sw, rank):
@@ -535,6 +580,10 @@ def run_ours(args):
 
     long_seqs = run_long(args, sw, torch, dev, rank) if args.long_steps > 0 else None
 
+    traceback = None
+    if args.align_top > 0:
+        traceback = run_traceback(args, sw, w, db, d_ti.cpu().numpy(), qlens)
+
     cpu = None
     if not args.no_cpu and world == 1 and rank == 0:
         threads = os.cpu_count() or 1
@@ -554,6 +603,7 @@ def run_ours(args):
         "batched": batched,
         "served": served,
         "long_sequences": long_seqs,
+        "traceback": traceback,
         "sharded_top_k": merged,
         "tuning": tuning,
         "per_query": per_query,

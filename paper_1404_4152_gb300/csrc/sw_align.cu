@@ -101,23 +101,37 @@ __device__ void run_dp(const AlignArgs& a, const int32_t* sM, uint2* bnd0, uint6
         uint32_t code_out = kPadCode, ex_out = 0;
         const uint2* bin = bnd0 + (p & 1) * half + kT;
         uint2* bout = bnd0 + ((p + 1) & 1) * half + kT;
+        // lane t holds the code and top-row entry of column s0 + t for the current block of
+        // 32 steps and of the next one; lane 0 takes them with a shuffle
+        auto code_at = [&](uint32_t j) -> uint32_t {
+            uint32_t c = j < cols ? df(j) : kPadCode;
+            return c > kPadCode ? kPadCode : c;
+        };
+        const uint2 kBorder = make_uint2((uint32_t)border, MODE == 2 ? ((uint32_t)border << 1)
+                                                                     : (uint32_t)border);
+        auto top_at = [&](uint32_t j) -> uint2 { return (p > 0 && j < cols) ? bin[j] : kBorder; };
+        uint32_t cblk = code_at(t), cnext = code_at(32 + t);
+        uint2 tblk = top_at(t), tnext = top_at(32 + t);
         for (uint32_t s = 0; s < steps; ++s) {
+            const uint32_t k = s & 31u;
+            if (k == 0 && s > 0) {
+                cblk = cnext;
+                tblk = tnext;
+                cnext = code_at(s + 32 + t);
+                tnext = top_at(s + 32 + t);
+            }
+            const uint32_t c0 = __shfl_sync(0xffffffffu, cblk, k);
+            const uint32_t t0x = __shfl_sync(0xffffffffu, tblk.x, k);
+            const uint32_t t0y = __shfl_sync(0xffffffffu, tblk.y, k);
             int32_t h_in = (int32_t)__shfl_up_sync(0xffffffffu, (uint32_t)hb_out, 1);
             int32_t e_in = (int32_t)__shfl_up_sync(0xffffffffu, (uint32_t)eb_out, 1);
             uint32_t code = __shfl_up_sync(0xffffffffu, code_out, 1);
             uint32_t ex = __shfl_up_sync(0xffffffffu, ex_out, 1);
             if (t == 0) {
-                code = s < cols ? df(s) : kPadCode;
-                if (code > kPadCode) code = kPadCode;
-                h_in = border;
-                e_in = border;
-                ex = 0;
-                if (p > 0 && s < cols) {
-                    const uint2 v = bin[s];
-                    h_in = (int32_t)v.x;
-                    e_in = MODE == 2 ? ((int32_t)v.y >> 1) : (int32_t)v.y;
-                    ex = MODE == 2 ? (v.y & 1u) : 0u;
-                }
+                code = c0;
+                h_in = (int32_t)t0x;
+                e_in = MODE == 2 ? ((int32_t)t0y >> 1) : (int32_t)t0y;
+                ex = MODE == 2 ? (t0y & 1u) : 0u;
             }
             code_out = code;
             const int64_t j = (int64_t)s - t;
@@ -336,27 +350,17 @@ extern "C" sw_status sw_align(sw_db* db, const uint8_t* query, uint32_t qlen, co
     DeviceScope scope(db->device);
     if ((st = stage_query(db, query, qlen, matrix))) return st;
 
-    // scratch: per-warp boundary rows, the hits, and (per batch) box bytes and ops
-    const uint64_t bstride = 2ull * (((uint64_t)std::max(db->max_len, qlen) + kT + 8 + 3) & ~3ull);
+    // scratch (grow-only buffers of the handle): per-warp rows, the hit table, and per
+    // batch the box bytes and the op strings
+    const uint64_t bstride = 2ull * (((uint64_t)db->max_len + kT + 8 + 3) & ~3ull);
     const uint64_t warp_bytes = bstride * sizeof(uint2);
     const int grid = (int)std::max<uint64_t>(
         1, std::min<uint64_t>({(uint64_t)db->nsm * 2, (n + kWarps - 1) / kWarps,
                                (256ull << 20) / (warp_bytes * kWarps) + 1}));
-    void* d_bnd = nullptr;
-    AlignHit* d_hits = nullptr;
-    cudaError_t e;
-    if ((e = db_malloc(db, &d_bnd, (size_t)grid * kWarps * warp_bytes)) != cudaSuccess)
-        return cuda_fail(e, "sw_align: scratch rows");
-    if ((e = db_malloc(db, (void**)&d_hits, n * sizeof(AlignHit))) != cudaSuccess) {
-        db_free(db, d_bnd, (size_t)grid * kWarps * warp_bytes);
-        return cuda_fail(e, "sw_align: hit table");
-    }
-    auto cleanup = [&](void* dir, size_t dir_bytes, void* dops, size_t ops_bytes) {
-        if (dir) db_free(db, dir, dir_bytes);
-        if (dops) db_free(db, dops, ops_bytes);
-        db_free(db, d_hits, n * sizeof(AlignHit));
-        db_free(db, d_bnd, (size_t)grid * kWarps * warp_bytes);
-    };
+    if ((st = ensure(db, db->a_rows, (size_t)grid * kWarps * warp_bytes, "sw_align: scratch rows")) ||
+        (st = ensure(db, db->a_hits, n * sizeof(AlignHit), "sw_align: hit table")))
+        return st;
+    AlignHit* const d_hits = (AlignHit*)db->a_hits.p;
     AlignArgs a{};
     a.tile_data = db->d_tile_data;
     a.tile_off = db->d_tile_off;
@@ -367,14 +371,13 @@ extern "C" sw_status sw_align(sw_db* db, const uint8_t* query, uint32_t qlen, co
     a.alpha = alpha;
     a.beta = beta;
     a.hits = d_hits;
-    a.boundary = (uint2*)d_bnd;
+    a.boundary = (uint2*)db->a_rows.p;
     a.bstride = bstride;
+    cudaError_t e;
     // phase 0: scores, end and start cells of every hit
     if ((e = cudaMemcpyAsync(d_hits, hits.data(), n * sizeof(AlignHit), cudaMemcpyHostToDevice,
-                             db->stream)) != cudaSuccess) {
-        cleanup(nullptr, 0, nullptr, 0);
+                             db->stream)) != cudaSuccess)
         return cuda_fail(e, "sw_align: upload");
-    }
     a.first = 0;
     a.count = n;
     a.phase = 0;
@@ -382,66 +385,56 @@ extern "C" sw_status sw_align(sw_db* db, const uint8_t* query, uint32_t qlen, co
     if ((e = cudaGetLastError()) != cudaSuccess ||
         (e = cudaMemcpyAsync(hits.data(), d_hits, n * sizeof(AlignHit), cudaMemcpyDeviceToHost,
                              db->stream)) != cudaSuccess ||
-        (e = cudaStreamSynchronize(db->stream)) != cudaSuccess) {
-        cleanup(nullptr, 0, nullptr, 0);
+        (e = cudaStreamSynchronize(db->stream)) != cudaSuccess)
         return cuda_fail(e, "sw_align: score and end cells");
-    }
-    // phase 1 in batches whose box bytes fit the budget
+
+    // phase 1 in batches whose box bytes fit 1 GiB (a larger single box takes its size)
+    auto box_of = [](const AlignHit& h) -> uint64_t {
+        return h.score > 0 ? (uint64_t)(h.ie - h.is + 1) * (h.je - h.js + 1) : 0;
+    };
     const uint64_t kDirBudget = 1ull << 30;
-    uint64_t max_box = 0;
-    for (auto& h : hits)
-        if (h.score > 0)
-            max_box = std::max<uint64_t>(max_box, (uint64_t)(h.ie - h.is + 1) * (h.je - h.js + 1));
-    const uint64_t dir_cap = std::max<uint64_t>(std::max<uint64_t>(max_box, kDirBudget), 256);
-    uint64_t ops_cap_dev = 0;
-    for (auto& h : hits)
-        if (h.score > 0) ops_cap_dev += (uint64_t)(h.ie - h.is + 1) + (h.je - h.js + 1);
-    ops_cap_dev = std::max<uint64_t>(ops_cap_dev, 256);
-    void* d_dir = nullptr;
-    char* d_ops = nullptr;
-    if ((e = db_malloc(db, &d_dir, dir_cap)) != cudaSuccess) {
-        cleanup(nullptr, 0, nullptr, 0);
-        return cuda_fail(e, "sw_align: traceback bytes");
-    }
-    if ((e = db_malloc(db, (void**)&d_ops, ops_cap_dev)) != cudaSuccess) {
-        cleanup(d_dir, dir_cap, nullptr, 0);
-        return cuda_fail(e, "sw_align: op strings");
-    }
-    uint64_t ops_off = 0;
+    uint64_t ops_total = 0;
     for (auto& h : hits) {
-        h.ops_off = ops_off;
-        if (h.score > 0) ops_off += (uint64_t)(h.ie - h.is + 1) + (h.je - h.js + 1);
+        h.ops_off = ops_total;
+        if (h.score > 0) ops_total += (uint64_t)(h.ie - h.is + 1) + (h.je - h.js + 1);
     }
+    std::vector<std::pair<uint32_t, uint32_t>> batches;
+    uint64_t dir_need = 0;
     for (uint32_t b0 = 0; b0 < n;) {
         uint64_t used = 0;
         uint32_t b1 = b0;
         for (; b1 < n; ++b1) {
-            const AlignHit& h = hits[b1];
-            const uint64_t box = h.score > 0 ? (uint64_t)(h.ie - h.is + 1) * (h.je - h.js + 1) : 0;
-            if (b1 > b0 && used + box > dir_cap) break;
+            const uint64_t box = (box_of(hits[b1]) + 15) & ~15ull;
+            if (b1 > b0 && used + box > kDirBudget) break;
             hits[b1].dir_off = used;
-            used += (box + 15) & ~15ull;
+            used += box;
         }
-        if ((e = cudaMemcpyAsync(d_hits + b0, hits.data() + b0, (b1 - b0) * sizeof(AlignHit),
-                                 cudaMemcpyHostToDevice, db->stream)) != cudaSuccess)
-            break;
-        a.first = b0;
-        a.count = b1 - b0;
-        a.phase = 1;
-        a.dir = (uint8_t*)d_dir;
-        a.ops = d_ops;
-        align_kernel<<<grid, kThreads, 0, db->stream>>>(a);
-        if ((e = cudaGetLastError()) != cudaSuccess) break;
+        batches.push_back({b0, b1});
+        dir_need = std::max(dir_need, used);
         b0 = b1;
+    }
+    if ((st = ensure(db, db->a_dir, std::max<uint64_t>(dir_need, 256), "sw_align: traceback bytes")) ||
+        (st = ensure(db, db->a_ops, std::max<uint64_t>(ops_total, 256), "sw_align: op strings")))
+        return st;
+    a.dir = (uint8_t*)db->a_dir.p;
+    a.ops = (char*)db->a_ops.p;
+    a.phase = 1;
+    e = cudaMemcpyAsync(d_hits, hits.data(), n * sizeof(AlignHit), cudaMemcpyHostToDevice,
+                        db->stream);
+    for (size_t bi = 0; bi < batches.size() && e == cudaSuccess; ++bi) {
+        a.first = batches[bi].first;
+        a.count = batches[bi].second - batches[bi].first;
+        align_kernel<<<grid, kThreads, 0, db->stream>>>(a);
+        e = cudaGetLastError();
     }
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(hits.data(), d_hits, n * sizeof(AlignHit), cudaMemcpyDeviceToHost,
                             db->stream);
-    std::vector<char> host_ops(ops_off);
-    if (e == cudaSuccess && ops_off)
-        e = cudaMemcpyAsync(host_ops.data(), d_ops, ops_off, cudaMemcpyDeviceToHost, db->stream);
+    std::vector<char> host_ops(ops_total);
+    if (e == cudaSuccess && ops_total)
+        e = cudaMemcpyAsync(host_ops.data(), db->a_ops.p, ops_total, cudaMemcpyDeviceToHost,
+                            db->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(db->stream);
-    cleanup(d_dir, dir_cap, d_ops, ops_cap_dev);
     if (e != cudaSuccess) return cuda_fail(e, "sw_align: traceback");
     uint64_t total = 0;
     for (auto& h : hits) {

@@ -113,7 +113,8 @@ void release(sw_db* db) {
     if (db->h_pinned) cudaFreeHost(db->h_pinned);
     if (db->graph.exec) cudaGraphExecDestroy(db->graph.exec);
     for (DevBuf* b : {&db->b_pairs, &db->b_qoff, &db->b_qlen, &db->b_flags, &db->b_topk,
-                      &db->b_queries, &db->b_scores, &db->b_top})
+                      &db->b_queries, &db->b_scores, &db->b_top, &db->a_rows, &db->a_hits,
+                      &db->a_dir, &db->a_ops})
         db_free(db, b->p, b->cap);
     for (auto& t : db->pending) { cudaEventDestroy(t.a); cudaEventDestroy(t.b); }
     for (auto ev : db->event_pool) cudaEventDestroy(ev);
