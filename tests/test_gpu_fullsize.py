@@ -53,3 +53,21 @@ def test_long_sequences_and_planted_duplicates(scale):
         assert set(ti.tolist()) <= set(int(p) for p in planted)
         if scale > 1:
             assert scores[planted].min() > 32767
+
+
+def test_traceback_of_planted_long_pairs_above_16_bits():
+    """Config 4b (matrix and penalties x3): alignments of planted 5,478-residue near-copies
+    whose scores pass the 16-bit range, letter for letter against the oracle."""
+    w = synth.config4(scale=3)
+    q = w.queries[0]
+    planted = np.asarray(w.notes["planted"][:6], dtype=np.uint64)
+    rng = np.random.default_rng(5)
+    others = rng.integers(0, w.n_seqs, size=6).astype(np.uint64)
+    idx = np.concatenate([planted, others])
+    with sw.sw_db_load(w.residues, w.offsets, long_threshold=3000) as db:
+        got = sw.sw_align(db, q, w.matrix, w.alpha, w.beta, idx)
+    for g, i in zip(got, idx):
+        d = w.residues[int(w.offsets[i]):int(w.offsets[i + 1])]
+        e = oracle.align(q, d, w.matrix, w.alpha, w.beta)
+        assert all(g[k] == e[k] for k in e), (int(i), g["score"], e["score"])
+    assert min(g["score"] for g in got[:6]) > 32767
