@@ -114,6 +114,21 @@ typedef struct {
 sw_status sw_db_load(const uint8_t* residues, const uint64_t* offsets, uint64_t n_seqs,
                      uint32_t alphabet, const sw_db_opts* opts, sw_db** out);
 
+/*
+ * Save a loaded database (its length-sorted tiles and index: the offline index
+ * of Section III) to a file, and open such a file later without sorting or
+ * re-tiling. The file is little-endian and written by this library; sw_db_open
+ * checks its magic, version, size and internal consistency (every sequence
+ * once in the sorted order, lengths and tile sizes adding up, every byte a
+ * residue code below the alphabet or the pad code) and fails with
+ * SW_ERR_INVALID_ARG otherwise. The long-sequence threshold is the one the
+ * database was loaded with (opts->long_threshold is ignored); device,
+ * device_budget and flags come from opts (NULL = defaults). Searches on an
+ * opened database give the same results as on the original.
+ */
+sw_status sw_db_save(const sw_db* db, const char* path);
+sw_status sw_db_open(const char* path, const sw_db_opts* opts, sw_db** out);
+
 /* Release a database and all its device memory. NULL is ignored. */
 void sw_db_free(sw_db* db);
 

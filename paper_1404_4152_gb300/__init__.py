@@ -105,6 +105,8 @@ _P, _U8, _U32, _U64, _I32 = (ctypes.c_void_p, ctypes.c_uint8, ctypes.c_uint32, c
 SIGNATURES = {
     "sw_db_load": (ctypes.c_int, [_P, _P, _U64, _U32, _P, ctypes.POINTER(_P)]),
     "sw_db_free": (None, [_P]),
+    "sw_db_save": (ctypes.c_int, [_P, ctypes.c_char_p]),
+    "sw_db_open": (ctypes.c_int, [ctypes.c_char_p, _P, ctypes.POINTER(_P)]),
     "sw_db_get_info": (ctypes.c_int, [_P, _P]),
     "sw_search": (ctypes.c_int, [_P, _P, _U32, _P, _I32, _I32, _U32, _P, _P, _P, _P, _P]),
     "sw_search_device": (ctypes.c_int, [_P, _P, _U32, _P, _I32, _I32, _U32, _P, _P, _P, _P]),
@@ -202,6 +204,22 @@ def sw_db_load(residues, offsets, alphabet: int = 20, device: int = 0, long_thre
 
 def sw_db_free(db: Database):
     db.free()
+
+
+def sw_db_save(db: Database, path: str):
+    """Write the loaded database (sorted tiles and index) to ``path``."""
+    _check(load_library().sw_db_save(db.handle, str(path).encode()))
+
+
+def sw_db_open(path: str, device: int = 0, device_budget: int = 0, flags: int = 0) -> Database:
+    """Open a database written by sw_db_save (no sorting or tiling)."""
+    opts = sw_db_opts(device, 0, device_budget, flags)
+    h = ctypes.c_void_p()
+    _check(load_library().sw_db_open(str(path).encode(), ctypes.byref(opts), ctypes.byref(h)))
+    db = Database(h, 0, 0)
+    info = db.info()
+    db.n_seqs, db.alphabet = info["n_seqs"], info["alphabet"]
+    return db
 
 
 def sw_db_get_info(db: Database) -> dict:

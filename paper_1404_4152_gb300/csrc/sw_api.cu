@@ -333,3 +333,205 @@ extern "C" sw_status sw_db_get_info(const sw_db* db, sw_db_info* info) {
     info->device = db->device;
     return SW_OK;
 }
+
+// ---------------------------------------------------------------------------
+// saving and reopening a loaded database (the offline index of Section III)
+// ---------------------------------------------------------------------------
+
+namespace {
+
+// File layout (little-endian, as written by this library): the header below,
+// then n_seqs uint32 sequence lengths (original order), n_tiles * 8 uint32
+// sorted ids (sorted position -> original index, UINT32_MAX for empty slots),
+// n_tiles uint32 tile lengths, and tile_bytes of tile data. Tile offsets are
+// the running sums of tile length x 8.
+struct DbFileHeader {
+    char magic[8];  // "SWGBDB01"
+    uint32_t version, alphabet;
+    uint64_t n_seqs, total_residues;
+    uint32_t max_len, long_threshold;
+    uint64_t n_tiles, n_long_tiles, n_long, tile_bytes, residues_short, residues_long;
+    uint32_t max_len_long, max_len_short;
+};
+constexpr char kDbMagic[8] = {'S', 'W', 'G', 'B', 'D', 'B', '0', '1'};
+constexpr uint64_t kIoChunk = 64ull << 20;
+
+bool write_all(FILE* f, const void* p, size_t n) { return n == 0 || fwrite(p, 1, n, f) == n; }
+bool read_all(FILE* f, void* p, size_t n) { return n == 0 || fread(p, 1, n, f) == n; }
+
+}  // namespace
+
+extern "C" sw_status sw_db_save(const sw_db* db, const char* path) {
+    clear_error();
+    if (!db || !path) return fail(SW_ERR_INVALID_ARG, "sw_db_save: NULL argument");
+    DevicePin pin(db->device);
+    if (!pin.ok) return fail(SW_ERR_CUDA, "sw_db_save: cannot select device %d", db->device);
+    DbFileHeader h{};
+    std::memcpy(h.magic, kDbMagic, 8);
+    h.version = 1;
+    h.alphabet = db->alphabet;
+    h.n_seqs = db->n_seqs;
+    h.total_residues = db->total_residues;
+    h.max_len = db->max_len;
+    h.long_threshold = db->long_threshold;
+    h.n_tiles = db->n_tiles;
+    h.n_long_tiles = db->n_long_tiles;
+    h.n_long = db->n_long;
+    h.tile_bytes = db->tile_bytes;
+    h.residues_short = db->residues_short;
+    h.residues_long = db->residues_long;
+    h.max_len_long = db->max_len_long;
+    h.max_len_short = db->max_len_short;
+    std::vector<uint32_t> sorted(db->n_tiles * kTileSeqs);
+    cudaError_t e = cudaMemcpy(sorted.data(), db->d_sorted, sorted.size() * 4, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "sw_db_save: sorted ids");
+    FILE* f = fopen(path, "wb");
+    if (!f) return fail(SW_ERR_INVALID_ARG, "sw_db_save: cannot open %s for writing", path);
+    bool ok = write_all(f, &h, sizeof h) && write_all(f, db->seq_len.data(), db->n_seqs * 4) &&
+              write_all(f, sorted.data(), sorted.size() * 4) &&
+              write_all(f, db->tile_len_host.data(), db->n_tiles * 4);
+    std::vector<uint8_t> buf;
+    for (uint64_t o = 0; ok && o < db->tile_bytes; o += kIoChunk) {
+        const uint64_t n = std::min(kIoChunk, db->tile_bytes - o);
+        buf.resize(n);
+        if ((e = cudaMemcpy(buf.data(), db->d_tile_data + o, n, cudaMemcpyDeviceToHost)) != cudaSuccess)
+            break;
+        ok = write_all(f, buf.data(), n);
+    }
+    const bool closed = fclose(f) == 0;
+    if (e != cudaSuccess) return cuda_fail(e, "sw_db_save: tiles");
+    if (!ok || !closed) return fail(SW_ERR_INVALID_ARG, "sw_db_save: write to %s failed", path);
+    return SW_OK;
+}
+
+extern "C" sw_status sw_db_open(const char* path, const sw_db_opts* opts, sw_db** out) {
+    clear_error();
+    if (!out || !path) return fail(SW_ERR_INVALID_ARG, "sw_db_open: NULL argument");
+    *out = nullptr;
+    FILE* f = fopen(path, "rb");
+    if (!f) return fail(SW_ERR_INVALID_ARG, "sw_db_open: cannot open %s", path);
+    DbFileHeader h{};
+    auto bad = [&](const char* why) {
+        fclose(f);
+        return fail(SW_ERR_INVALID_ARG, "sw_db_open: %s: %s", path, why);
+    };
+    if (!read_all(f, &h, sizeof h) || std::memcmp(h.magic, kDbMagic, 8) != 0 || h.version != 1)
+        return bad("not a database file of this library");
+    if (h.alphabet == 0 || h.alphabet > SW_MAX_ALPHABET || h.n_seqs == 0 ||
+        h.n_seqs >= 0xffffffffull || h.n_tiles != (h.n_seqs + kTileSeqs - 1) / kTileSeqs ||
+        h.n_long_tiles > h.n_tiles)
+        return bad("inconsistent header");
+    // the file must hold exactly the arrays the header announces
+    const uint64_t expect = sizeof h + h.n_seqs * 4 + h.n_tiles * kTileSeqs * 4 + h.n_tiles * 4 +
+                            h.tile_bytes;
+    if (fseek(f, 0, SEEK_END) != 0 || (uint64_t)ftell(f) != expect ||
+        fseek(f, (long)sizeof h, SEEK_SET) != 0)
+        return bad("size does not match its header");
+    sw_db* db = new (std::nothrow) sw_db();
+    if (!db) {
+        fclose(f);
+        return fail(SW_ERR_OOM, "sw_db_open: host allocation failed");
+    }
+    auto fail_db = [&](sw_status st) {
+        fclose(f);
+        release(db);
+        return st;
+    };
+    db->device = opts ? opts->device : 0;
+    db->alphabet = h.alphabet;
+    db->n_seqs = h.n_seqs;
+    db->total_residues = h.total_residues;
+    db->max_len = h.max_len;
+    db->long_threshold = h.long_threshold;  // the tiles were binned with it
+    db->budget = opts ? opts->device_budget : 0;
+    db->flags = opts ? opts->flags : 0;
+    db->n_tiles = h.n_tiles;
+    db->n_long_tiles = h.n_long_tiles;
+    db->n_long = h.n_long;
+    db->tile_bytes = h.tile_bytes;
+    db->residues_short = h.residues_short;
+    db->residues_long = h.residues_long;
+    db->max_len_long = h.max_len_long;
+    db->max_len_short = h.max_len_short;
+    db->seq_len.resize(h.n_seqs);
+    std::vector<uint32_t> sorted(h.n_tiles * kTileSeqs);
+    db->tile_len_host.resize(h.n_tiles);
+    if (!read_all(f, db->seq_len.data(), h.n_seqs * 4) || !read_all(f, sorted.data(), sorted.size() * 4) ||
+        !read_all(f, db->tile_len_host.data(), h.n_tiles * 4))
+        return fail_db(fail(SW_ERR_INVALID_ARG, "sw_db_open: %s: short read", path));
+    // cross-checks: every sequence once in the sorted order, tile sizes add up
+    db->pos_of.assign(h.n_seqs, 0xffffffffu);
+    uint64_t seen = 0, residues = 0, tile_sum = 0;
+    uint32_t max_len = 0;
+    for (uint64_t p = 0; p < sorted.size(); ++p) {
+        const uint32_t s = sorted[p];
+        if (s == 0xffffffffu) continue;
+        if (s >= h.n_seqs || db->pos_of[s] != 0xffffffffu)
+            return fail_db(fail(SW_ERR_INVALID_ARG, "sw_db_open: %s: bad sorted ids", path));
+        db->pos_of[s] = (uint32_t)p;
+        ++seen;
+        if (db->seq_len[s] > db->tile_len_host[p / kTileSeqs])
+            return fail_db(fail(SW_ERR_INVALID_ARG, "sw_db_open: %s: tile shorter than a sequence", path));
+    }
+    for (uint64_t s = 0; s < h.n_seqs; ++s) {
+        residues += db->seq_len[s];
+        max_len = std::max(max_len, db->seq_len[s]);
+    }
+    std::vector<uint64_t> tile_off(h.n_tiles);
+    for (uint64_t t = 0; t < h.n_tiles; ++t) {
+        tile_off[t] = tile_sum;
+        tile_sum += (uint64_t)db->tile_len_host[t] * kTileSeqs;
+    }
+    if (seen != h.n_seqs || residues != h.total_residues || max_len != h.max_len ||
+        tile_sum != h.tile_bytes)
+        return fail_db(fail(SW_ERR_INVALID_ARG, "sw_db_open: %s: arrays disagree with the header", path));
+
+    DevicePin pin(db->device);
+    if (!pin.ok) return fail_db(fail(SW_ERR_CUDA, "sw_db_open: cannot select device %d", db->device));
+    cudaError_t e;
+    if ((e = cudaStreamCreateWithFlags(&db->stream, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaEventCreate(&db->ev_t0)) != cudaSuccess ||
+        (e = cudaEventCreate(&db->ev_t1)) != cudaSuccess)
+        return fail_db(cuda_fail(e, "sw_db_open: stream/event creation"));
+    cudaDeviceProp prop;
+    cudaGetDeviceProperties(&prop, db->device);
+    db->nsm = prop.multiProcessorCount;
+    sw_status st;
+    if ((st = db_alloc(db, (void**)&db->d_misc, 64, "sw_db_open: counters")) ||
+        (st = db_alloc(db, (void**)&db->d_tile_data, db->tile_bytes, "sw_db_open: tiles")) ||
+        (st = db_alloc(db, (void**)&db->d_tile_off, h.n_tiles * 8, "sw_db_open: tile offsets")) ||
+        (st = db_alloc(db, (void**)&db->d_tile_len, h.n_tiles * 4, "sw_db_open: tile lengths")) ||
+        (st = db_alloc(db, (void**)&db->d_sorted, sorted.size() * 4, "sw_db_open: sorted ids")) ||
+        (st = db_alloc(db, (void**)&db->d_scores, h.n_seqs * 4, "sw_db_open: score buffer")))
+        return fail_db(st);
+    e = cudaMemcpy(db->d_tile_off, tile_off.data(), h.n_tiles * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(db->d_tile_len, db->tile_len_host.data(), h.n_tiles * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(db->d_sorted, sorted.data(), sorted.size() * 4, cudaMemcpyHostToDevice);
+    std::vector<uint8_t> buf;
+    for (uint64_t o = 0; e == cudaSuccess && o < db->tile_bytes; o += kIoChunk) {
+        const uint64_t n = std::min(kIoChunk, db->tile_bytes - o);
+        buf.resize(n);
+        if (!read_all(f, buf.data(), n))
+            return fail_db(fail(SW_ERR_INVALID_ARG, "sw_db_open: %s: short read", path));
+        // every byte is a residue code below the alphabet or the pad code
+        for (uint64_t k = 0; k < n; ++k)
+            if (buf[k] >= db->alphabet && buf[k] != kPadCode)
+                return fail_db(fail(SW_ERR_INVALID_ARG, "sw_db_open: %s: bad residue code", path));
+        e = cudaMemcpy(db->d_tile_data + o, buf.data(), n, cudaMemcpyHostToDevice);
+    }
+    fclose(f);
+    f = nullptr;
+    if (e != cudaSuccess) {
+        st = cuda_fail(e, "sw_db_open: upload");
+        release(db);
+        return st;
+    }
+    if ((st = sw_db_prepare_search(db))) {
+        release(db);
+        return st;
+    }
+    *out = db;
+    return SW_OK;
+}
