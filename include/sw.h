@@ -395,6 +395,17 @@ sw_status sw_align(sw_db* db, const uint8_t* query, uint32_t qlen, const int8_t*
                    int32_t alpha, int32_t beta, const uint64_t* db_index, uint32_t n,
                    sw_alignment* out, char* ops, uint64_t ops_cap, uint64_t* ops_used);
 
+/*
+ * Bounds-checked build (compiled with -DSW_DEBUG_BOUNDS, libswgb300_debug.so; a
+ * stand-in for a memory checker): the kernels check their shared- and
+ * global-memory indices, skip an access that would leave its buffer and record
+ * the site of the first such access in the handle. This call waits for the
+ * device, returns that site (0: none) and clears it. In the normal build it
+ * always returns 0. Sites: 1-8 search kernels, 11-13 rescoring, 21-25
+ * alignment.
+ */
+sw_status sw_db_debug_check(sw_db* db, uint32_t* site);
+
 /* Message for the last non-OK status returned to this thread ("" if none). */
 const char* sw_last_error(void);
 

@@ -125,6 +125,7 @@ SIGNATURES = {
     "sw_db_autotune": (ctypes.c_int, [_P, _P, _I32, _I32, ctypes.c_char_p, _P]),
     "sw_db_get_profile": (ctypes.c_int, [_P, _P]),
     "sw_db_reset_profile": (ctypes.c_int, [_P]),
+    "sw_db_debug_check": (ctypes.c_int, [_P, _P]),
     "sw_align": (ctypes.c_int, [_P, _P, _U32, _P, _I32, _I32, _P, _U32, _P, _P, _U64, _P]),
     "sw_last_error": (ctypes.c_char_p, []),
     "sw_version": (ctypes.c_char_p, []),
@@ -134,13 +135,14 @@ _lib = None
 
 
 def load_library(path: str | None = None):
-    """Load libswgb300.so (raises if it has not been built)."""
+    """Load libswgb300.so (raises if it has not been built); with SWGB_DEBUG_BOUNDS=1 in
+    the environment, the bounds-checked build libswgb300_debug.so instead."""
     global _lib
     if _lib is not None and path is None:
         return _lib
-    p = path or _build.lib_path()
+    p = path or _build.lib_path(debug=os.environ.get("SWGB_DEBUG_BOUNDS") == "1")
     if not os.path.exists(p):
-        raise ImportError(f"libswgb300.so is not built ({p}); run __graft_entry__.build()")
+        raise ImportError(f"{os.path.basename(p)} is not built ({p}); run __graft_entry__.build()")
     lib = ctypes.CDLL(p)
     for name, (res, args) in SIGNATURES.items():
         f = getattr(lib, name)
@@ -468,3 +470,11 @@ def sw_align(db: Database, query, matrix, alpha: int, beta: int, db_index):
                     "db_index": o.db_index, "d_begin": o.d_begin, "d_end": o.d_end,
                     "ops": raw[o.ops_offset:o.ops_offset + o.ops_len].decode()})
     return res
+
+
+def sw_db_debug_check(db: Database) -> int:
+    """Site of the first out-of-bounds device access the handle's kernels recorded since the
+    last check (0: none), then cleared; always 0 unless the bounds-checked build is loaded."""
+    site = ctypes.c_uint32(0)
+    _check(load_library().sw_db_debug_check(db.handle, ctypes.byref(site)))
+    return int(site.value)

@@ -17,6 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 INCLUDE = os.path.join(ROOT, "include")
 LIB_NAME = "libswgb300.so"
+DEBUG_LIB_NAME = "libswgb300_debug.so"  # built with -DSW_DEBUG_BOUNDS (checked accesses)
 
 SOURCES = ["sw_wavefront.cu", "sw_rescore.cu", "sw_topk.cu", "sw_api.cu", "sw_search.cu",
            "sw_noalloc.cu", "sw_server.cu", "sw_tune.cu", "sw_align.cu"]
@@ -32,8 +33,8 @@ def nvcc() -> str:
     return "nvcc"
 
 
-def lib_path() -> str:
-    return os.path.join(BUILD, LIB_NAME)
+def lib_path(debug: bool = False) -> str:
+    return os.path.join(BUILD, DEBUG_LIB_NAME if debug else LIB_NAME)
 
 
 def _digest(paths) -> str:
@@ -52,21 +53,24 @@ def _inputs():
     return files
 
 
-def build(verbose: bool = False, force: bool = False) -> str:
-    """Build the library if any source changed; returns the .so path."""
+def build(verbose: bool = False, force: bool = False, debug: bool = False) -> str:
+    """Build the library if any source changed; returns the .so path. ``debug`` builds
+    the bounds-checked variant (every checked device access records its site in an
+    error word and is skipped when out of bounds; see sw_db_debug_check)."""
     os.makedirs(BUILD, exist_ok=True)
-    stamp = os.path.join(BUILD, "stamp.txt")
-    digest = _digest(_inputs())
-    out = lib_path()
+    stamp = os.path.join(BUILD, "stamp_debug.txt" if debug else "stamp.txt")
+    extra = ["-DSW_DEBUG_BOUNDS"] if debug else []
+    digest = _digest(_inputs()) + ("-debug" if debug else "")
+    out = lib_path(debug)
     if not force and os.path.exists(out) and os.path.exists(stamp):
         if open(stamp).read().strip() == digest:
             return out
     cmds = []
     objs = []
     for src in SOURCES:
-        obj = os.path.join(BUILD, src.replace(".cu", ".o"))
+        obj = os.path.join(BUILD, src.replace(".cu", "_dbg.o" if debug else ".o"))
         objs.append(obj)
-        cmds.append([nvcc(), *ARCH, *FLAGS, "-I", INCLUDE, "-I", CSRC, "-c",
+        cmds.append([nvcc(), *ARCH, *FLAGS, *extra, "-I", INCLUDE, "-I", CSRC, "-c",
                      os.path.join(CSRC, src), "-o", obj])
 
     def run(cmd):

@@ -70,6 +70,8 @@ struct AlignArgs {
     uint8_t* dir;
     char* ops;
     int phase;          // 0: score, end and start cells; 1: box programme and traceback
+    uint32_t* dbg;      // error word of the bounds-checked build
+    uint64_t dir_cap;   // bytes of dir (checked)
 };
 
 __device__ __forceinline__ int32_t imax(int32_t a, int32_t b) { return a > b ? a : b; }
@@ -109,7 +111,9 @@ __device__ void run_dp(const AlignArgs& a, const int32_t* sM, uint2* bnd0, uint6
         };
         const uint2 kBorder = make_uint2((uint32_t)border, MODE == 2 ? ((uint32_t)border << 1)
                                                                      : (uint32_t)border);
-        auto top_at = [&](uint32_t j) -> uint2 { return (p > 0 && j < cols) ? bin[j] : kBorder; };
+        auto top_at = [&](uint32_t j) -> uint2 {
+            return (p > 0 && j < cols && sw_ok(kT + (uint64_t)j < half, a.dbg, 22)) ? bin[j] : kBorder;
+        };
         uint32_t cblk = code_at(t), cnext = code_at(32 + t);
         uint2 tblk = top_at(t), tnext = top_at(32 + t);
         for (uint32_t s = 0; s < steps; ++s) {
@@ -161,7 +165,8 @@ __device__ void run_dp(const AlignArgs& a, const int32_t* sM, uint2* bnd0, uint6
                             bi = i;
                             bj = (uint32_t)j;
                         }
-                    } else if (valid) {
+                    } else if (valid && sw_ok((uint64_t)i * cols + (uint64_t)j < (uint64_t)rows * cols,
+                                              a.dbg, 21)) {
                         const uint32_t hsel = (Mv >= E && Mv >= F) ? 0u : (E >= F ? 1u : 2u);
                         dir[(uint64_t)i * cols + (uint64_t)j] =
                             (uint8_t)(hsel | (ex << 2) | (((fx >> r) & 1u) << 3));
@@ -188,7 +193,8 @@ __device__ void run_dp(const AlignArgs& a, const int32_t* sM, uint2* bnd0, uint6
             eb_out = E;
             ex_out = ex;
             hdiag0 = h_in;
-            if (t == kT - 1 && p + 1 < P && j >= 0 && j < (int64_t)cols) {
+            if (t == kT - 1 && p + 1 < P && j >= 0 && j < (int64_t)cols &&
+                sw_ok(kT + (uint64_t)j < half, a.dbg, 23)) {
                 const uint32_t ev = MODE == 2 ? ((uint32_t)eb_out << 1) | ex_out : (uint32_t)eb_out;
                 bout[j] = make_uint2((uint32_t)hb_out, ev);
             }
@@ -215,8 +221,11 @@ __global__ void __launch_bounds__(kThreads) align_kernel(const AlignArgs a) {
         const uint64_t sp = hit.sp;
         const uint8_t* seq = a.tile_data + a.tile_off[sp / kTileSeqs] +
                              ((sp >> 1) & (kTilePairs - 1)) * 8 + (sp & 1);
-        auto dcode = [seq](uint32_t j) -> uint32_t { return seq[(size_t)(j >> 2) * 32 + (j & 3) * 2]; };
         const uint32_t n = hit.n;
+        uint32_t* const dbg = a.dbg;
+        auto dcode = [seq, n, dbg](uint32_t j) -> uint32_t {
+            return sw_ok(j < n, dbg, 25) ? seq[(size_t)(j >> 2) * 32 + (j & 3) * 2] : kPadCode;
+        };
         if (a.phase == 0) {
             int32_t best = 0;
             uint32_t bi = 0xffffffffu, bj = 0xffffffffu;
@@ -271,6 +280,10 @@ __global__ void __launch_bounds__(kThreads) align_kernel(const AlignArgs a) {
             }
             const uint32_t is = hit.is, js = hit.js;
             const uint32_t rows = hit.ie - is + 1, cols = hit.je - js + 1;
+            if (!sw_ok(hit.dir_off + (uint64_t)rows * cols <= a.dir_cap, a.dbg, 24)) {
+                if (t == 0) hit.ops_len = 0xffffffffu;
+                continue;
+            }
             uint8_t* dir = a.dir + hit.dir_off;
             int32_t unused = 0;
             uint32_t ui = 0, uj = 0;
@@ -373,6 +386,7 @@ extern "C" sw_status sw_align(sw_db* db, const uint8_t* query, uint32_t qlen, co
     a.hits = d_hits;
     a.boundary = (uint2*)db->a_rows.p;
     a.bstride = bstride;
+    a.dbg = db->d_counters + kDebugWord;
     cudaError_t e;
     // phase 0: scores, end and start cells of every hit
     if ((e = cudaMemcpyAsync(d_hits, hits.data(), n * sizeof(AlignHit), cudaMemcpyHostToDevice,
@@ -417,6 +431,7 @@ extern "C" sw_status sw_align(sw_db* db, const uint8_t* query, uint32_t qlen, co
         (st = ensure(db, db->a_ops, std::max<uint64_t>(ops_total, 256), "sw_align: op strings")))
         return st;
     a.dir = (uint8_t*)db->a_dir.p;
+    a.dir_cap = db->a_dir.cap;
     a.ops = (char*)db->a_ops.p;
     a.phase = 1;
     e = cudaMemcpyAsync(d_hits, hits.data(), n * sizeof(AlignHit), cudaMemcpyHostToDevice,

@@ -7,6 +7,28 @@
 
 namespace swgb {
 
+// Bounds-checked build (-DSW_DEBUG_BOUNDS; compute-sanitizer is not available on every
+// machine): sw_ok(cond, err, site) records the site of the first failed check in the
+// handle's error word and returns false so the caller skips the access. In the normal
+// build it is true and compiles away. Sites: 1-9 search kernels (query profile, ring,
+// stage, matrix table, boundary read / write, database stream), 11-13 rescoring, 21-26
+// alignment.
+#ifdef SW_DEBUG_BOUNDS
+constexpr bool kDebugBounds = true;
+#else
+constexpr bool kDebugBounds = false;
+#endif
+#ifdef __CUDACC__
+__device__ __forceinline__ bool sw_ok(bool cond, uint32_t* err, uint32_t site) {
+    if (kDebugBounds && !cond) {
+        if (err) atomicCAS(err, 0u, site);
+        return false;
+    }
+    return true;
+}
+#endif
+constexpr int kDebugWord = 60;  // index of the error word in the handle's counters
+
 // Residue code used for padding. Its profile row is all zeros, so padded
 // cells score 0 against everything (the dummy residue of the sequence
 // profile, Section III.B.1); codes from callers are always < 32.
@@ -74,6 +96,7 @@ struct WavefrontArgs {
     uint32_t flag_cap;
     // scheduling
     uint32_t* work_counter;
+    uint32_t* dbg;                  // error word of the bounds-checked build (may be NULL)
 };
 
 struct KernelChoice {
@@ -109,9 +132,10 @@ struct RescoreArgs {
     int32_t alpha, beta;
     int32_t* scores;
     uint64_t score_stride;
-    uint2* boundary;                // per warp slot
+    uint2* boundary;                // per block: one row of bstride entries
     uint64_t bstride;
     uint32_t* work_counter;
+    uint32_t* dbg;                  // error word of the bounds-checked build (may be NULL)
 };
 cudaError_t launch_rescore(const RescoreArgs& a, int grid, cudaStream_t stream);
 int rescore_block_threads();

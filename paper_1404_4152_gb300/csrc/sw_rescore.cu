@@ -116,13 +116,15 @@ __global__ void __launch_bounds__(kThreads) rescore_kernel(const RescoreArgs a) 
                 for (int h = 0; h < 2; ++h) {
                     const uint32_t j = c0 + (uint32_t)t + 32u * h;
                     uint32_t c = kPadCode;
-                    if (j < L) {
+                    if (j < L && sw_ok((j >> 2) * 32 + (j & 3) * 2 + ((sp >> 1) & (kTilePairs - 1)) * 8 +
+                                           (sp & 1) < (uint64_t)L * 8, a.dbg, 12)) {
                         c = stream[(size_t)(j >> 2) * 32 + (j & 3) * 2];
                         if (c > kPadCode) c = kPadCode;
                     }
                     sm.code[w][t + 32 * h] = (uint8_t)c;
                     if (w == 0)
-                        sm.top0[t + 32 * h] = (band > 0 && j < L) ? row7[j] : make_uint2(0, 0);
+                        sm.top0[t + 32 * h] = (band > 0 && j < L && sw_ok(j < a.bstride, a.dbg, 11))
+                                                  ? row7[j] : make_uint2(0, 0);
                 }
                 __syncwarp();
                 const uint32_t ring_base = round * nbp * kC;  // ring index of column 0 in this round
@@ -145,7 +147,8 @@ __global__ void __launch_bounds__(kThreads) rescore_kernel(const RescoreArgs a) 
                     int32_t diag = hdiag0, E = e_in;
 #pragma unroll
                     for (int l = 0; l < kR; ++l) {
-                        const int32_t sc = sm.M[qc[l] + code];
+                        int32_t sc = 0;
+                        if (sw_ok(qc[l] + code < (uint32_t)(kM * kM), a.dbg, 13)) sc = sm.M[qc[l] + code];
                         const int32_t H = LaneS32::max3_relu(diag + sc, E, Fr[l]);
                         diag = Hl[l];
                         Hl[l] = H;
@@ -162,7 +165,7 @@ __global__ void __launch_bounds__(kThreads) rescore_kernel(const RescoreArgs a) 
                         const uint2 v = make_uint2((uint32_t)hb_out, (uint32_t)eb_out);
                         if (w + 1 < kWarps)
                             sm.ring[w][(ring_base + (uint32_t)j) % kRing] = v;
-                        else
+                        else if (sw_ok((uint64_t)j < a.bstride, a.dbg, 11))
                             row7[j] = v;
                     }
                 }

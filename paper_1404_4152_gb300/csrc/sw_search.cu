@@ -270,6 +270,7 @@ WavefrontArgs base_args(sw_db* db, const int8_t* d_matrix, int32_t alpha, int32_
     a.bin[1].bstride = db->bstride_short;
     a.work_counter = db->d_counters + 0;
     a.flag_count = db->d_counters + 3;
+    a.dbg = db->d_counters + kDebugWord;
     return a;
 }
 
@@ -290,6 +291,7 @@ RescoreArgs rescore_args(sw_db* db, const int8_t* d_matrix, int32_t alpha, int32
     r.boundary = db->d_bnd_rescore;
     r.bstride = db->bstride_rescore;
     r.work_counter = db->d_counters + 2;
+    r.dbg = db->d_counters + kDebugWord;
     return r;
 }
 
@@ -777,5 +779,19 @@ extern "C" sw_status sw_search_batch(sw_db* db, uint32_t nq, const uint8_t* cons
             std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0)
                 .count();
     }
+    return SW_OK;
+}
+
+extern "C" sw_status sw_db_debug_check(sw_db* db, uint32_t* site) {
+    clear_error();
+    if (!db || !site) return fail(SW_ERR_INVALID_ARG, "sw_db_debug_check: NULL argument");
+    *site = 0;
+    if (!kDebugBounds) return SW_OK;
+    DeviceScope scope(db->device);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess)
+        e = cudaMemcpy(site, db->d_counters + kDebugWord, 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(db->d_counters + kDebugWord, 0, 4);
+    if (e != cudaSuccess) return cuda_fail(e, "sw_db_debug_check");
     return SW_OK;
 }

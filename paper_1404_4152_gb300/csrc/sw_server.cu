@@ -149,6 +149,7 @@ sw_status launch_items(sw_server* s, KernelChoice kc, const std::vector<QueryPai
                              s->stream)) != cudaSuccess)
         return cuda_fail(e, "server: wave upload");
     WavefrontArgs a{};
+    a.dbg = db->d_counters + kDebugWord;
     a.tile_data = db->d_tile_data;
     a.tile_off = db->d_tile_off;
     a.tile_len = db->d_tile_len;
@@ -253,6 +254,7 @@ sw_status run_wave(sw_server* s, std::vector<std::shared_ptr<Request>>& act) {
     if ((st = launch_items(s, ks, singles, sc0, sn, 1))) return st;
     if (!i32) {
         RescoreArgs r{};
+        r.dbg = db->d_counters + kDebugWord;
         r.tile_data = db->d_tile_data;
         r.tile_off = db->d_tile_off;
         r.tile_len = db->d_tile_len;

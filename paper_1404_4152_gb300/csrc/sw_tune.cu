@@ -141,6 +141,7 @@ extern "C" sw_status sw_db_autotune(sw_db* db, const int8_t* matrix, int32_t alp
                 if (!wavefront_supported(kc)) continue;
                 const uint32_t qlen = 8u * R * 4;  // four whole passes
                 WavefrontArgs a{};
+                a.dbg = db->d_counters + kDebugWord;
                 a.tile_data = db->d_tile_data;
                 a.tile_off = db->d_tile_off;
                 a.tile_len = db->d_tile_len;

@@ -309,7 +309,7 @@ __device__ __forceinline__ void process_chunk(const WavefrontArgs& a, const BinA
         uint4 bq0 = make_uint4(0, 0, 0, 0), bq1 = make_uint4(0, 0, 0, 0);
         if (t == 0 && blocks_real > 0) {
             wq = *reinterpret_cast<const uint2*>(stream);
-            if (read_bnd) {
+            if (read_bnd && sw_ok(kSkew * T + 4 <= half, a.dbg, 6)) {
                 bq0 = reinterpret_cast<const uint4*>(bnd_in)[0];
                 bq1 = reinterpret_cast<const uint4*>(bnd_in)[1];
             }
@@ -324,9 +324,9 @@ __device__ __forceinline__ void process_chunk(const WavefrontArgs& a, const BinA
             uint2 wn = make_uint2(kPadWord, kPadWord);
             uint4 bn0 = make_uint4(0, 0, 0, 0), bn1 = make_uint4(0, 0, 0, 0);
             const uint32_t nb = (s0 >> 2) + 1;
-            if (t == 0 && nb < blocks_real) {
+            if (t == 0 && nb < blocks_real && sw_ok((uint64_t)nb * 4 < L, a.dbg, 8)) {
                 wn = *reinterpret_cast<const uint2*>(stream + (size_t)nb * 32);
-                if (read_bnd) {
+                if (read_bnd && sw_ok(kSkew * T + s0 + 8 <= half, a.dbg, 6)) {
                     bn0 = reinterpret_cast<const uint4*>(bnd_in + s0 + 4)[0];
                     bn1 = reinterpret_cast<const uint4*>(bnd_in + s0 + 4)[1];
                 }
@@ -350,6 +350,8 @@ __device__ __forceinline__ void process_chunk(const WavefrontArgs& a, const BinA
                     }
                 }
                 typename Mode::template Cols<T, R> cs;
+                if (!sw_ok((code_cur & 0xffu) < kProfileRows && (code_cur >> 8) < kProfileRows, a.dbg, 1))
+                    code_cur = kPair ? kPadPair : kPadCode;
                 cs.load(prof, code_cur, t);
                 V diag = hdiag0;
                 V E = e_cur;
@@ -372,7 +374,8 @@ __device__ __forceinline__ void process_chunk(const WavefrontArgs& a, const BinA
                 h_cur = h_nxt;
                 e_cur = e_nxt;
                 code_cur = code_nxt;
-                if (t == T - 1)  // column s - 2 (T-1), at entry 2T + that >= 2
+                if (t == T - 1 &&  // column s - 2 (T-1), at entry 2T + that >= 2
+                    sw_ok((uint64_t)(kSkew * T + s0 + k - kSkew * (T - 1)) < half, a.dbg, 7))
                     bnd_out[(int)(s0 + k) - kSkew * (T - 1)] =
                         make_uint2((uint32_t)hb_out, (uint32_t)eb_out);
             }
@@ -547,6 +550,9 @@ __device__ __forceinline__ void process_chunk_ring(const WavefrontArgs& a, const
     const uint32_t smem_s = (uint32_t)__cvta_generic_to_shared(smem);
     const uint32_t ring_s = smem_s + kRingOffset + (uint32_t)warp * (A + 1) * kCodeBytes + g * 4;
     const uint32_t stage_s = smem_s + kMtBytes + (uint32_t)(warp * 4 + g) * kStageWords * 4;
+    // this warp's ring and this group's stage (checked in the bounds-checked build)
+    const uint32_t ring_lo = ring_s - g * 4, ring_hi = ring_lo + (A + 1) * kCodeBytes;
+    auto in_ring = [&](uint32_t addr) { return addr >= ring_lo && addr + 4 <= ring_hi; };
     const uint32_t* const mt = reinterpret_cast<const uint32_t*>(smem);
 
     const V vbeta = Lane::splat(-a.beta);
@@ -613,7 +619,8 @@ __device__ __forceinline__ void process_chunk_ring(const WavefrontArgs& a, const
         const bool read_bnd = p > 0;
         // boundary entry of column bcol of the next block (threads below kRingBlock stage it)
         uint2 bnext = make_uint2(0, 0);
-        if (t < kRingBlock && read_bnd && bcol < L) bnext = bnd_in[bcol];
+        if (t < kRingBlock && read_bnd && bcol < L && sw_ok(S * T + bcol < half, a.dbg, 6))
+            bnext = bnd_in[bcol];
         if constexpr (S == 2) {
             if (t == 0) {  // column 0
                 h_cur = bnext.x;
@@ -626,7 +633,10 @@ __device__ __forceinline__ void process_chunk_ring(const WavefrontArgs& a, const
             {
                 const uint32_t j = s0 + bcol;
                 uint32_t pc = kPadPair;
-                if (j < L) pc = *reinterpret_cast<const uint16_t*>(stream + (size_t)(j >> 2) * 32 + (j & 3) * 2);
+                if (j < L && sw_ok((j >> 2) * 32 + ((sp >> 1) & (kTilePairs - 1)) * 8 + (j & 3) * 2 + 2 <=
+                                       (uint64_t)L * 8, a.dbg, 8))
+                    pc = *reinterpret_cast<const uint16_t*>(stream + (size_t)(j >> 2) * 32 + (j & 3) * 2);
+                if (!sw_ok((pc & 0xffu) < kProfileRows && (pc >> 8) < kProfileRows, a.dbg, 5)) pc = kPadPair;
                 const uint32_t* const ma = mt + (pc & 0xffu);
                 const uint32_t* const mb = mt + (pc >> 8);
                 bool dup;
@@ -643,8 +653,10 @@ __device__ __forceinline__ void process_chunk_ring(const WavefrontArgs& a, const
                             if (whole || c < A) {
                                 const uint32_t v = prmt(wa, wb, b | ((8u | b) << 4) |
                                                                   ((4u + b) << 8) | ((12u + b) << 12));
-                                sts_u32(at + c * kCodeBytes, v);
-                                if (dup) sts_u32(at + c * kCodeBytes + W * kSlot, v);
+                                if (sw_ok(in_ring(at + c * kCodeBytes), a.dbg, 3))
+                                    sts_u32(at + c * kCodeBytes, v);
+                                if (dup && sw_ok(in_ring(at + c * kCodeBytes + W * kSlot), a.dbg, 3))
+                                    sts_u32(at + c * kCodeBytes + W * kSlot, v);
                             }
                         }
                     }
@@ -657,8 +669,10 @@ __device__ __forceinline__ void process_chunk_ring(const WavefrontArgs& a, const
                         const uint32_t wa = ma[k * kProfileRows], wb = mb[k * kProfileRows];
                         if (c < A) {
                             const uint32_t v = prmt(wa, wb, bsel);
-                            sts_u32(at + c * kCodeBytes, v);
-                            if (dup) sts_u32(at + c * kCodeBytes + W * kSlot, v);
+                            if (sw_ok(in_ring(at + c * kCodeBytes), a.dbg, 3))
+                                sts_u32(at + c * kCodeBytes, v);
+                            if (dup && sw_ok(in_ring(at + c * kCodeBytes + W * kSlot), a.dbg, 3))
+                                sts_u32(at + c * kCodeBytes + W * kSlot, v);
                         }
                     }
                 }
@@ -668,15 +682,18 @@ __device__ __forceinline__ void process_chunk_ring(const WavefrontArgs& a, const
                 // (both planes for S = 2)
                 const uint32_t at = ring_s + (W - T + 1 + (uint32_t)t) * kSlot;
                 for (uint32_t c = 0; c < A; ++c) {
-                    sts_u32(at + c * kCodeBytes, 0u);
-                    if constexpr (S == 2) sts_u32(at + c * kCodeBytes + Geo::kPlane, 0u);
+                    if (sw_ok(in_ring(at + c * kCodeBytes), a.dbg, 3)) sts_u32(at + c * kCodeBytes, 0u);
+                    if constexpr (S == 2)
+                        if (sw_ok(in_ring(at + c * kCodeBytes + Geo::kPlane), a.dbg, 3))
+                            sts_u32(at + c * kCodeBytes + Geo::kPlane, 0u);
                 }
             }
             if (t < kRingBlock) sts_u64(stage_s + (uint32_t)t * 8, bnext);
             __syncwarp();  // this block's columns and boundary entries are visible
             if (t < kRingBlock) {
                 const uint32_t jn = s0 + kRingBlock + (uint32_t)t;
-                bnext = (read_bnd && jn < L) ? bnd_in[jn] : make_uint2(0, 0);
+                bnext = (read_bnd && jn < L && sw_ok(S * T + jn < half, a.dbg, 6)) ? bnd_in[jn]
+                                                                                 : make_uint2(0, 0);
             }
             uint2* const bo = bnd_out + (int)s0 - S * (T - 1);
 #pragma unroll
@@ -709,7 +726,8 @@ __device__ __forceinline__ void process_chunk_ring(const WavefrontArgs& a, const
                 V E = e_in;
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
-                    const V sc = lds_u32(cur[r] + koff);
+                    V sc = 0;
+                    if (sw_ok(in_ring(cur[r] + koff), a.dbg, 2)) sc = lds_u32(cur[r] + koff);
                     const V x = Lane::vadd(diag, sc);              // H[i-1][j-1] + fsbt
                     const V H = Lane::max3_relu(x, E, Fr[r]);      // H[i][j]
                     diag = Hl[r];
@@ -722,7 +740,10 @@ __device__ __forceinline__ void process_chunk_ring(const WavefrontArgs& a, const
                 hb_out = Hl[R - 1];
                 eb_out = E;
                 hdiag0 = h_in;
-                if (t == T - 1) bo[k] = make_uint2((uint32_t)hb_out, (uint32_t)eb_out);
+                if (t == T - 1 && sw_ok((int64_t)(S * T) + (int64_t)(s0 + k) - S * (T - 1) >= 0 &&
+                                            (uint64_t)(S * T + s0 + k - S * (T - 1)) < half,
+                                        a.dbg, 7))
+                    bo[k] = make_uint2((uint32_t)hb_out, (uint32_t)eb_out);
             }
             // next block: slots advance by kAdvance, wrapping at W
             const uint32_t blk = ((s0 / S) - (uint32_t)t) & (W - 1);
