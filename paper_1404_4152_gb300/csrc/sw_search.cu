@@ -166,6 +166,8 @@ sw_status ensure(sw_db* db, DevBuf& b, size_t bytes, const char* what) {
 sw_status sw_db_prepare_search(sw_db* db) {
     sw_status st;
     if ((st = db_alloc(db, (void**)&db->d_counters, 256, "search counters"))) return st;
+    if (cudaMemset(db->d_counters, 0, 256) != cudaSuccess)  // includes the error word
+        return fail(SW_ERR_CUDA, "search counters: memset failed");
     const int warps = wavefront_block_threads() / 32;
     db->grid_short = db->nsm * occupancy_max(all_choices());
     if (db->n_long_tiles < db->n_tiles) {
