@@ -396,6 +396,16 @@ sw_status sw_align(sw_db* db, const uint8_t* query, uint32_t qlen, const int8_t*
                    sw_alignment* out, char* ops, uint64_t ops_cap, uint64_t* ops_used);
 
 /*
+ * The same for the hits of several queries in one call (all pairs aligned in
+ * parallel): queries (HOST) concatenated with qoffsets[0..nq] as in
+ * sw_search_batch; hit k aligns query hit_query[k] with db_index[k].
+ */
+sw_status sw_align_batch(sw_db* db, uint32_t nq, const uint8_t* queries, const uint64_t* qoffsets,
+                         const int8_t* matrix, int32_t alpha, int32_t beta,
+                         const uint32_t* hit_query, const uint64_t* db_index, uint32_t n,
+                         sw_alignment* out, char* ops, uint64_t ops_cap, uint64_t* ops_used);
+
+/*
  * Bounds-checked build (compiled with -DSW_DEBUG_BOUNDS, libswgb300_debug.so; a
  * stand-in for a memory checker): the kernels check their shared- and
  * global-memory indices, skip an access that would leave its buffer and record

@@ -127,6 +127,8 @@ SIGNATURES = {
     "sw_db_reset_profile": (ctypes.c_int, [_P]),
     "sw_db_debug_check": (ctypes.c_int, [_P, _P]),
     "sw_align": (ctypes.c_int, [_P, _P, _U32, _P, _I32, _I32, _P, _U32, _P, _P, _U64, _P]),
+    "sw_align_batch": (ctypes.c_int, [_P, _U32, _P, _P, _P, _I32, _I32, _P, _P, _U32, _P, _P, _U64,
+                                      _P]),
     "sw_last_error": (ctypes.c_char_p, []),
     "sw_version": (ctypes.c_char_p, []),
 }
@@ -478,3 +480,29 @@ def sw_db_debug_check(db: Database) -> int:
     site = ctypes.c_uint32(0)
     _check(load_library().sw_db_debug_check(db.handle, ctypes.byref(site)))
     return int(site.value)
+
+
+def sw_align_batch(db: Database, queries, matrix, alpha: int, beta: int, hits):
+    """Alignments for several queries in one call: ``hits`` is a sequence of (query number,
+    database index) pairs; returns one dict per hit, as sw_align."""
+    qs = [np.ascontiguousarray(q, dtype=np.uint8) for q in queries]
+    cat = np.concatenate(qs) if qs else np.zeros(0, np.uint8)
+    qoff = np.zeros(len(qs) + 1, dtype=np.uint64)
+    qoff[1:] = np.cumsum([q.size for q in qs])
+    m = np.ascontiguousarray(matrix, dtype=np.int8)
+    hq = np.ascontiguousarray([h[0] for h in hits], dtype=np.uint32)
+    hi = np.ascontiguousarray([h[1] for h in hits], dtype=np.uint64)
+    n = int(hi.size)
+    out = (sw_alignment * max(n, 1))()
+    used = ctypes.c_uint64(0)
+    maxq = max([q.size for q in qs] + [0])
+    cap = max(1, n * (int(maxq) + int(db.info()["max_length"])))
+    ops = ctypes.create_string_buffer(cap)
+    _check(load_library().sw_align_batch(db.handle, len(qs), _ptr(cat), _ptr(qoff), _ptr(m),
+                                         int(alpha), int(beta), _ptr(hq), _ptr(hi), n, out, ops,
+                                         cap, ctypes.byref(used)))
+    raw = ops.raw
+    return [{"score": out[k].score, "q_begin": out[k].q_begin, "q_end": out[k].q_end,
+             "db_index": out[k].db_index, "d_begin": out[k].d_begin, "d_end": out[k].d_end,
+             "ops": raw[out[k].ops_offset:out[k].ops_offset + out[k].ops_len].decode()}
+            for k in range(n)]

@@ -47,7 +47,8 @@ constexpr int32_t kNeg = -(1 << 29);  // minus infinity for the anchored program
 struct AlignHit {
     uint64_t sp;        // sorted position of the sequence
     uint32_t n;         // its length
-    uint32_t pad0;
+    uint32_t q_len;     // the query: length and offset in the concatenated queries
+    uint64_t q_off;
     int32_t score;      // phase 0 outputs
     uint32_t ie, je, is, js;
     uint32_t ops_len;   // phase 1 output (0xffffffff: inconsistent bytes, see below)
@@ -58,8 +59,7 @@ struct AlignHit {
 struct AlignArgs {
     const uint8_t* tile_data;
     const uint64_t* tile_off;
-    const uint8_t* query;
-    uint32_t qlen;
+    const uint8_t* query;   // concatenated queries (AlignHit::q_off)
     const int8_t* matrix;
     uint32_t alphabet;
     int32_t alpha, beta;
@@ -214,10 +214,10 @@ __global__ void __launch_bounds__(kThreads) align_kernel(const AlignArgs a) {
     const uint64_t nwarps = (uint64_t)gridDim.x * kWarps;
     uint2* const bnd0 = a.boundary + slot * a.bstride;
     const uint64_t half = a.bstride / 2;
-    const uint8_t* q = a.query;
-
     for (uint64_t h = a.first + slot; h < (uint64_t)a.first + a.count; h += nwarps) {
         AlignHit& hit = a.hits[h];
+        const uint8_t* q = a.query + hit.q_off;
+        const uint32_t qlen = hit.q_len;
         const uint64_t sp = hit.sp;
         const uint8_t* seq = a.tile_data + a.tile_off[sp / kTileSeqs] +
                              ((sp >> 1) & (kTilePairs - 1)) * 8 + (sp & 1);
@@ -229,8 +229,8 @@ __global__ void __launch_bounds__(kThreads) align_kernel(const AlignArgs a) {
         if (a.phase == 0) {
             int32_t best = 0;
             uint32_t bi = 0xffffffffu, bj = 0xffffffffu;
-            if (a.qlen && n)
-                run_dp<0>(a, sM, bnd0, half, t, a.qlen, n, [q](uint32_t i) -> uint32_t { return q[i]; },
+            if (qlen && n)
+                run_dp<0>(a, sM, bnd0, half, t, qlen, n, [q](uint32_t i) -> uint32_t { return q[i]; },
                           dcode, 0, best, bi, bj, nullptr);
             // first maximal cell over the warp
 #pragma unroll
@@ -340,29 +340,15 @@ __global__ void __launch_bounds__(kThreads) align_kernel(const AlignArgs a) {
 
 using namespace swgb;
 
-extern "C" sw_status sw_align(sw_db* db, const uint8_t* query, uint32_t qlen, const int8_t* matrix,
-                              int32_t alpha, int32_t beta, const uint64_t* db_index, uint32_t n,
-                              sw_alignment* out, char* ops, uint64_t ops_cap, uint64_t* ops_used) {
-    clear_error();
-    sw_status st;
-    if ((st = check_common(db, qlen, alpha, beta, 0, "sw_align"))) return st;
-    if ((st = validate_host_query(db, query, qlen, matrix, "sw_align"))) return st;
-    if (n && (!db_index || !out)) return fail(SW_ERR_INVALID_ARG, "sw_align: NULL db_index or out");
-    if (!ops_used) return fail(SW_ERR_INVALID_ARG, "sw_align: NULL ops_used");
-    *ops_used = 0;
-    if (n == 0) return SW_OK;
-    std::vector<AlignHit> hits(n);
-    for (uint32_t k = 0; k < n; ++k) {
-        if (db_index[k] >= db->n_seqs)
-            return fail(SW_ERR_INVALID_ARG, "sw_align: db_index %llu out of range",
-                        (unsigned long long)db_index[k]);
-        std::memset(&hits[k], 0, sizeof(AlignHit));
-        hits[k].sp = db->pos_of[db_index[k]];
-        hits[k].n = db->seq_len[db_index[k]];
-    }
-    DeviceScope scope(db->device);
-    if ((st = stage_query(db, query, qlen, matrix))) return st;
+namespace {
 
+// Shared by sw_align and sw_align_batch: hits[k].q_off / q_len / sp / n are set, the
+// queries and the matrix are on the device at d_queries / db->d_matrix.
+sw_status align_hits(sw_db* db, const uint8_t* d_queries, int32_t alpha, int32_t beta,
+                     std::vector<AlignHit>& hits, const uint64_t* db_index, sw_alignment* out,
+                     char* ops, uint64_t ops_cap, uint64_t* ops_used) {
+    sw_status st;
+    const uint32_t n = (uint32_t)hits.size();
     // scratch (grow-only buffers of the handle): per-warp rows, the hit table, and per
     // batch the box bytes and the op strings
     const uint64_t bstride = 2ull * (((uint64_t)db->max_len + kT + 8 + 3) & ~3ull);
@@ -377,8 +363,7 @@ extern "C" sw_status sw_align(sw_db* db, const uint8_t* query, uint32_t qlen, co
     AlignArgs a{};
     a.tile_data = db->d_tile_data;
     a.tile_off = db->d_tile_off;
-    a.query = db->d_query;
-    a.qlen = qlen;
+    a.query = d_queries;
     a.matrix = db->d_matrix;
     a.alphabet = db->alphabet;
     a.alpha = alpha;
@@ -477,4 +462,85 @@ extern "C" sw_status sw_align(sw_db* db, const uint8_t* query, uint32_t qlen, co
         pos += h.ops_len;
     }
     return SW_OK;
+}
+
+sw_status make_hits(const sw_db* db, const uint64_t* db_index, uint32_t n, const char* fn,
+                    std::vector<AlignHit>& hits) {
+    hits.assign(n, AlignHit{});
+    for (uint32_t k = 0; k < n; ++k) {
+        if (db_index[k] >= db->n_seqs)
+            return fail(SW_ERR_INVALID_ARG, "%s: db_index %llu out of range", fn,
+                        (unsigned long long)db_index[k]);
+        hits[k].sp = db->pos_of[db_index[k]];
+        hits[k].n = db->seq_len[db_index[k]];
+    }
+    return SW_OK;
+}
+
+}  // namespace
+
+extern "C" sw_status sw_align(sw_db* db, const uint8_t* query, uint32_t qlen, const int8_t* matrix,
+                              int32_t alpha, int32_t beta, const uint64_t* db_index, uint32_t n,
+                              sw_alignment* out, char* ops, uint64_t ops_cap, uint64_t* ops_used) {
+    clear_error();
+    sw_status st;
+    if ((st = check_common(db, qlen, alpha, beta, 0, "sw_align"))) return st;
+    if ((st = validate_host_query(db, query, qlen, matrix, "sw_align"))) return st;
+    if (n && (!db_index || !out)) return fail(SW_ERR_INVALID_ARG, "sw_align: NULL db_index or out");
+    if (!ops_used) return fail(SW_ERR_INVALID_ARG, "sw_align: NULL ops_used");
+    *ops_used = 0;
+    if (n == 0) return SW_OK;
+    std::vector<AlignHit> hits;
+    if ((st = make_hits(db, db_index, n, "sw_align", hits))) return st;
+    for (auto& h : hits) {
+        h.q_off = 0;
+        h.q_len = qlen;
+    }
+    DeviceScope scope(db->device);
+    if ((st = stage_query(db, query, qlen, matrix))) return st;
+    return align_hits(db, db->d_query, alpha, beta, hits, db_index, out, ops, ops_cap, ops_used);
+}
+
+extern "C" sw_status sw_align_batch(sw_db* db, uint32_t nq, const uint8_t* queries,
+                                    const uint64_t* qoffsets, const int8_t* matrix, int32_t alpha,
+                                    int32_t beta, const uint32_t* hit_query, const uint64_t* db_index,
+                                    uint32_t n, sw_alignment* out, char* ops, uint64_t ops_cap,
+                                    uint64_t* ops_used) {
+    clear_error();
+    sw_status st;
+    if ((st = check_common(db, 1, alpha, beta, 0, "sw_align_batch"))) return st;
+    if (!qoffsets || !queries || !matrix)
+        return fail(SW_ERR_INVALID_ARG, "sw_align_batch: NULL queries, offsets or matrix");
+    if (n && (!db_index || !hit_query || !out))
+        return fail(SW_ERR_INVALID_ARG, "sw_align_batch: NULL hit_query, db_index or out");
+    if (!ops_used) return fail(SW_ERR_INVALID_ARG, "sw_align_batch: NULL ops_used");
+    *ops_used = 0;
+    for (uint32_t q = 0; q < nq; ++q)
+        if (qoffsets[q + 1] <= qoffsets[q] || qoffsets[q + 1] - qoffsets[q] > 0x7fffffffull)
+            return fail(SW_ERR_INVALID_ARG, "sw_align_batch: query %u is empty or offsets are bad", q);
+    const uint64_t total = qoffsets[nq] - qoffsets[0];
+    for (uint64_t i = 0; i < total; ++i)
+        if (queries[qoffsets[0] + i] >= db->alphabet)
+            return fail(SW_ERR_INVALID_ARG, "sw_align_batch: query code %u is not below alphabet %u",
+                        queries[qoffsets[0] + i], db->alphabet);
+    if (n == 0) return SW_OK;
+    std::vector<AlignHit> hits;
+    if ((st = make_hits(db, db_index, n, "sw_align_batch", hits))) return st;
+    for (uint32_t k = 0; k < n; ++k) {
+        if (hit_query[k] >= nq)
+            return fail(SW_ERR_INVALID_ARG, "sw_align_batch: hit_query %u out of range", hit_query[k]);
+        hits[k].q_off = qoffsets[hit_query[k]] - qoffsets[0];
+        hits[k].q_len = (uint32_t)(qoffsets[hit_query[k] + 1] - qoffsets[hit_query[k]]);
+    }
+    DeviceScope scope(db->device);
+    cudaError_t e;
+    if ((st = ensure(db, db->b_queries, std::max<uint64_t>(total, 16), "sw_align_batch: queries")))
+        return st;
+    if ((e = cudaMemcpyAsync(db->b_queries.p, queries + qoffsets[0], total, cudaMemcpyHostToDevice,
+                             db->stream)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(db->d_matrix, matrix, (size_t)db->alphabet * db->alphabet,
+                             cudaMemcpyHostToDevice, db->stream)) != cudaSuccess)
+        return cuda_fail(e, "sw_align_batch: upload");
+    return align_hits(db, (const uint8_t*)db->b_queries.p, alpha, beta, hits, db_index, out, ops,
+                      ops_cap, ops_used);
 }

@@ -86,3 +86,20 @@ def test_scores_beyond_16_bits_and_edge_cases():
         assert got[0]["score"] > 32767 and got[3]["score"] == 0 and got[3]["ops"] == ""
         assert got[5] == got[0]
         assert sw.sw_align(db, q, M, 8, 88, np.zeros(0, np.uint64)) == []
+
+
+def test_batch_of_queries_matches_single_calls():
+    w = synth.config0()
+    qs = synth.make_queries([144, 700, 37, 1500], 41)
+    with sw.sw_db_load(w.residues, w.offsets) as db:
+        hits, singles = [], []
+        for i, q in enumerate(qs):
+            _, _, ti, _ = sw.sw_search(db, q, w.matrix, w.alpha, w.beta, 7, want_scores=False)
+            hits += [(i, int(x)) for x in ti]
+            singles += sw.sw_align(db, q, w.matrix, w.alpha, w.beta, ti)
+        got = sw.sw_align_batch(db, qs, w.matrix, w.alpha, w.beta, hits)
+    assert got == singles
+    for (i, x), g in zip(hits[::5], got[::5]):
+        e = oracle.align(qs[i], w.residues[int(w.offsets[x]):int(w.offsets[x + 1])], w.matrix,
+                         w.alpha, w.beta)
+        assert all(g[k] == e[k] for k in e)
