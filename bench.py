@@ -57,7 +57,7 @@ PAPER_PHI_GCUPS_MAX = 58.8    # SWAPHI InterSP, one Xeon Phi 5110P, TrEMBL (Sect
 # profiles/search_kernel_ring_807x600k_ncu.md), valid for the kernel source whose sha256
 # starts with TRAFFIC_SOURCE.
 TRAFFIC_BYTES_PER_CELL = 0.0186
-TRAFFIC_SOURCE = "98ce66b7fb1686fc"
+TRAFFIC_SOURCE = "67527f3a46af2ca1"
 
 
 def parse_args():
