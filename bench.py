@@ -58,6 +58,10 @@ PAPER_PHI_GCUPS_MAX = 58.8    # SWAPHI InterSP, one Xeon Phi 5110P, TrEMBL (Sect
 # starts with TRAFFIC_SOURCE.
 TRAFFIC_BYTES_PER_CELL = 0.0186
 TRAFFIC_SOURCE = "67527f3a46af2ca1"
+# ALU instructions per row update of that kernel in the same capture (VIADDMNMX, VIMNMX3,
+# PRMT, ISETP, LOP3, SHF, SEL, ... from sass__inst_executed_per_opcode): the instruction
+# mix the kernel actually executes, against the 3.5 minimum
+ALU_OPS_PER_CELL_MEASURED = 3.92
 
 
 def parse_args():
@@ -540,6 +544,9 @@ def run_ours(args):
     roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "Gop/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "dram_gbs": traffic / (mean_ms / 1e3) / 1e9 if traffic else None,
+                "measured_mix": ({"alu_ops_per_cell": ALU_OPS_PER_CELL_MEASURED,
+                                  "frac": achieved / ALU_OPS_PER_CELL * ALU_OPS_PER_CELL_MEASURED / peak}
+                                 if same_kernel else None),
                 "per_unit": f"{ALU_OPS_PER_CELL} integer ALU lane-ops per DP cell (minimum); "
                             f"{cells_per_launch:.4g} cells per launch, mean launch {mean_ms:.2f} ms",
                 "peak_basis": f"{nsm} SMs x {sm_mhz:.0f} MHz (sampled) x {ALU_LANES_PER_CLK_SM} ALU "
