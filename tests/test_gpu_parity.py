@@ -227,3 +227,37 @@ def test_device_budget_gives_oom():
     with pytest.raises(sw.SwError) as e:
         sw.sw_db_load(res, off, device_budget=4096)
     assert e.value.status == "SW_ERR_OOM"
+
+
+def test_two_handles_from_two_threads():
+    """Different handles are independent: searched at the same time from two host threads
+    they give the results each gives alone (the binding releases the GIL in C calls)."""
+    import threading
+
+    lens_a = synth.gen_lengths(3000, synth.db_qtable(), 101, 1)
+    lens_b = synth.gen_lengths(2000, synth.db_qtable(), 102, 1)
+    ra, oa = _db_from_lengths(lens_a, 101)
+    rb, ob = _db_from_lengths(lens_b, 102)
+    qs = synth.make_queries([90, 400, 1200], 103)
+    with sw.sw_db_load(ra, oa) as da, sw.sw_db_load(rb, ob) as db_:
+        alone = {(n, i): sw.sw_search(d, q, synth.BLOSUM62, 1, 11, 10)[0]
+                 for n, d in (("a", da), ("b", db_)) for i, q in enumerate(qs)}
+        got, errors = {}, []
+
+        def work(name, d):
+            try:
+                for _ in range(3):
+                    for i, q in enumerate(qs):
+                        got[(name, i)] = sw.sw_search(d, q, synth.BLOSUM62, 1, 11, 10)[0]
+            except Exception as e:  # reported below
+                errors.append(e)
+
+        ts = [threading.Thread(target=work, args=("a", da)), threading.Thread(target=work, args=("b", db_))]
+        for t in ts:
+            t.start()
+        for t in ts:
+            t.join()
+    assert not errors, errors
+    for key, v in alone.items():
+        assert np.array_equal(got[key], v), key
+    assert np.array_equal(alone[("a", 1)], oracle.scores(qs[1], ra, oa, synth.BLOSUM62, 1, 11))
