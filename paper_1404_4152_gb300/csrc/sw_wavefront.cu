@@ -627,15 +627,21 @@ __device__ __forceinline__ void process_chunk_ring(const WavefrontArgs& a, const
                 e_cur = bnext.y;
             }
         }
+        // the codes of the column this thread builds, loaded one block ahead
+        auto codes_at = [&](uint32_t j) -> uint32_t {
+            if (j < L && sw_ok((j >> 2) * 32 + ((sp >> 1) & (kTilePairs - 1)) * 8 + (j & 3) * 2 + 2 <=
+                                   (uint64_t)L * 8, a.dbg, 8))
+                return *reinterpret_cast<const uint16_t*>(stream + (size_t)(j >> 2) * 32 + (j & 3) * 2);
+            return kPadPair;
+        };
+        uint32_t pc_next = codes_at(bcol);
 
         for (uint32_t s0 = 0; s0 < steps; s0 += kRingBlock) {
             __syncwarp();  // the slots rewritten below are no longer read
             {
                 const uint32_t j = s0 + bcol;
-                uint32_t pc = kPadPair;
-                if (j < L && sw_ok((j >> 2) * 32 + ((sp >> 1) & (kTilePairs - 1)) * 8 + (j & 3) * 2 + 2 <=
-                                       (uint64_t)L * 8, a.dbg, 8))
-                    pc = *reinterpret_cast<const uint16_t*>(stream + (size_t)(j >> 2) * 32 + (j & 3) * 2);
+                uint32_t pc = pc_next;
+                pc_next = codes_at(j + kRingBlock);
                 if (!sw_ok((pc & 0xffu) < kProfileRows && (pc >> 8) < kProfileRows, a.dbg, 5)) pc = kPadPair;
                 const uint32_t* const ma = mt + (pc & 0xffu);
                 const uint32_t* const mb = mt + (pc >> 8);
