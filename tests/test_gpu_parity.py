@@ -87,7 +87,7 @@ def test_long_sequence_kernel(threshold, kflags):
         _check(db, res, off, q, synth.BLOSUM62, 1, 11, 10)
 
 
-@pytest.mark.parametrize("A", [4, 20, 24, 32])
+@pytest.mark.parametrize("A", [1, 2, 4, 20, 21, 24, 32])
 @pytest.mark.parametrize("ab", [(1, 11), (0, 5), (5, 2), (0, 0), (3, 0), (2, 12)])
 def test_alphabets_and_penalties(A, ab, kflags):
     rng = np.random.default_rng(A * 100 + ab[0] * 10 + ab[1])
