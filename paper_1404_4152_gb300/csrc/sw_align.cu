@@ -4,7 +4,8 @@
 // future work; a database search reports them for its top hits. Three
 // dynamic programmes per (query, sequence) pair, in int32, each a lane
 // wavefront of one warp (lane t on column s - t at step s, kR query rows per
-// lane, passes of 256 rows with the bottom row kept in the warp's scratch):
+// lane, passes of 32 kR rows with the bottom row kept in the warp's scratch;
+// a block is one warp, so the hits spread over every SM):
 //
 //  1. recurrence (1) with the score S and the end cell: the first (i, j), in
 //     order of i then j, whose H equals S;
@@ -36,10 +37,11 @@ namespace swgb {
 
 namespace {
 
-constexpr int kWarps = 8;
+constexpr int kWarps = 1;  // one warp per block: the hits spread over every SM
 constexpr int kThreads = kWarps * 32;
+constexpr int kBlocksPerSm = 12;
 constexpr int kT = 32;
-constexpr int kR = 8;
+constexpr int kR = 12;
 constexpr int kRows = kT * kR;
 constexpr int kM = kProfileRows;
 constexpr int32_t kNeg = -(1 << 29);  // minus infinity for the anchored programmes
@@ -354,7 +356,7 @@ sw_status align_hits(sw_db* db, const uint8_t* d_queries, int32_t alpha, int32_t
     const uint64_t bstride = 2ull * (((uint64_t)db->max_len + kT + 8 + 3) & ~3ull);
     const uint64_t warp_bytes = bstride * sizeof(uint2);
     const int grid = (int)std::max<uint64_t>(
-        1, std::min<uint64_t>({(uint64_t)db->nsm * 2, (n + kWarps - 1) / kWarps,
+        1, std::min<uint64_t>({(uint64_t)db->nsm * kBlocksPerSm, (n + kWarps - 1) / kWarps,
                                (256ull << 20) / (warp_bytes * kWarps) + 1}));
     if ((st = ensure(db, db->a_rows, (size_t)grid * kWarps * warp_bytes, "sw_align: scratch rows")) ||
         (st = ensure(db, db->a_hits, n * sizeof(AlignHit), "sw_align: hit table")))
