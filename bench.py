@@ -56,12 +56,12 @@ PAPER_PHI_GCUPS_MAX = 58.8    # SWAPHI InterSP, one Xeon Phi 5110P, TrEMBL (Sect
 # per thread (ncu dram__bytes_read + _write on a 600,000-sequence case;
 # profiles/search_kernel_ring_807x600k_ncu.md), valid for the kernel source whose sha256
 # starts with TRAFFIC_SOURCE.
-TRAFFIC_BYTES_PER_CELL = 0.0182
-TRAFFIC_SOURCE = "abe771cdb5e9ce1f"
-# ALU instructions per row update of that kernel in the same capture (VIADDMNMX, VIMNMX3,
-# PRMT, ISETP, LOP3, SHF, SEL, ... from sass__inst_executed_per_opcode): the instruction
-# mix the kernel actually executes, against the 3.5 minimum
-ALU_OPS_PER_CELL_MEASURED = 3.93
+TRAFFIC_BYTES_PER_CELL = 0.0187
+TRAFFIC_SOURCE = "5481cce112a758ca"
+# ALU instructions per row update of that kernel in the same capture (ALU-pipe instructions
+# over row updates: VIADDMNMX, VIMNMX3, PRMT, ISETP, LOP3, ...; the 807-row query's last
+# pass of 8 rows per thread included): the mix the kernel executes, against the 3.5 minimum
+ALU_OPS_PER_CELL_MEASURED = 4.06
 
 
 def parse_args():

@@ -50,6 +50,17 @@ constexpr int kLongT = 32;
 constexpr int kLongR = 16;
 constexpr int kTuneR = 5;  // rows-per-lane choices: 8, 12, 16, 20, 24
 
+// The single-query ring kernel with 24 rows per thread runs floor(m / 192) whole passes
+// of an m-row query and covers the rest (rem rows) with one pass of the fewest rows per
+// thread among 8, 16 and 24 that holds them; 0 when nothing is left.
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+constexpr int ring_last_rows(uint32_t rem) {
+    return rem == 0 ? 0 : rem <= (uint32_t)kShortT * 8 ? 8 : rem <= (uint32_t)kShortT * 16 ? 16 : 24;
+}
+constexpr int kRingLastR = 24;  // the rows per thread of the kernel that does so
+
 // One bin of units: pairs of sequences (single-query packed kernels) or
 // single sequences (batched and int32 kernels) at sorted positions
 // first_unit.., plus the bin's scratch rows.

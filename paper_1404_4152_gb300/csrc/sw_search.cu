@@ -35,19 +35,34 @@ constexpr uint64_t kRescoreScratch = 256ull << 20;
 
 const int kShortR[] = {8, 12, 16, 20, 24};
 
-// Rows padded to whole passes times the cost of a row: measured by the
-// autotuner when the handle has been tuned, else estimated as alu_per_row ALU
-// instructions per query row plus about 8 per step; summed over the items.
+// The cost of one pass of 8 R query rows: the autotuner's time per row and residue, else
+// alu_per_row ALU instructions per row plus about 8 per step.
+double pass_cost(const sw_db* db, int mode, int R, double alu_per_row) {
+    const double measured = db->tuned ? db->tuning.ns_per_row_residue[mode][(R - 8) / 4] : 0.0;
+    return measured > 0 ? measured * kShortT * R : (alu_per_row * R + 8.0);
+}
+
+// The cost of an m-row query with R rows per thread: whole passes, except that the ring
+// kernel with kRingLastR rows per thread ends with one shorter pass (ring_last_rows).
+double rows_cost(const sw_db* db, int mode, uint32_t m, int R, double alu_per_row) {
+    const uint32_t TR = (uint32_t)kShortT * R;
+    if (mode == KernelChoice::kPairRing && R == kRingLastR) {
+        const int last = ring_last_rows(m % TR);
+        return (double)(m / TR) * pass_cost(db, mode, R, alu_per_row) +
+               (last ? pass_cost(db, mode, last, alu_per_row) : 0.0);
+    }
+    return (double)((m + TR - 1) / TR) * pass_cost(db, mode, R, alu_per_row);
+}
+
+// The rows per thread of the least total cost over the items (padded rows included).
 int choose_R(const sw_db* db, int mode, const std::vector<uint32_t>& lengths, double alu_per_row) {
     int bestR = 16;
     double best = 1e300;
     for (int i = 0; i < (int)(sizeof kShortR / sizeof kShortR[0]); ++i) {
         const int R = kShortR[i];
-        const uint32_t TR = (uint32_t)kShortT * R;
         const double measured = db->tuned ? db->tuning.ns_per_row_residue[mode][i] : 0.0;
-        const double per_pass = measured > 0 ? measured * TR : (alu_per_row * R + 8.0);
         double cost = 0;
-        for (uint32_t m : lengths) cost += (double)((m + TR - 1) / TR) * per_pass;
+        for (uint32_t m : lengths) cost += rows_cost(db, mode, m, R, alu_per_row);
         if (measured <= 0 && R == 16) cost *= 0.97;
         if (cost < best) { best = cost; bestR = R; }
     }
@@ -66,12 +81,10 @@ KernelChoice single_choice(const sw_db* db, uint32_t qlen, bool i32) {
     if (db->flags & SW_DB_FLAG_QUERY_PROFILE) return qp;
     const KernelChoice ring{KernelChoice::kPairRing, choose_R(db, 3, {qlen}, 3.9)};
     if (!db->tuned) return ring;
-    auto cost = [&](const KernelChoice& k) {
-        const uint32_t TR = (uint32_t)kShortT * k.R;
-        const int i = (k.R - 8) / 4;
-        return (double)((qlen + TR - 1) / TR) * TR * db->tuning.ns_per_row_residue[k.mode][i];
-    };
-    return cost(qp) < cost(ring) ? qp : ring;
+    return rows_cost(db, KernelChoice::kPairDb, qlen, qp.R, 4.5) <
+                   rows_cost(db, KernelChoice::kPairRing, qlen, ring.R, 3.9)
+               ? qp
+               : ring;
 }
 
 // Two halves per slot, each the longest unit plus the wavefront's slack.

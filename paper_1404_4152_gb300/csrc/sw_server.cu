@@ -247,10 +247,11 @@ sw_status run_wave(sw_server* s, std::vector<std::shared_ptr<Request>>& act) {
     sw_status st;
     if ((st = launch_items(s, KernelChoice{KernelChoice::kQueryPair, 16}, pairs, pc0, pn, 0)))
         return st;
+    // lone queries: the ring with 24 rows per thread, whose short last pass fits any length
     const KernelChoice ks = i32 ? KernelChoice{KernelChoice::kInt32, 16}
-                          : KernelChoice{(db->flags & SW_DB_FLAG_QUERY_PROFILE) ? KernelChoice::kPairDb
-                                                                                : KernelChoice::kPairRing,
-                                         16};
+                          : (db->flags & SW_DB_FLAG_QUERY_PROFILE)
+                              ? KernelChoice{KernelChoice::kPairDb, 16}
+                              : KernelChoice{KernelChoice::kPairRing, kRingLastR};
     if ((st = launch_items(s, ks, singles, sc0, sn, 1))) return st;
     if (!i32) {
         RescoreArgs r{};
@@ -448,7 +449,7 @@ extern "C" sw_status sw_server_create(sw_db* db, const sw_server_opts* opts, sw_
     }
     cudaError_t e;
     const KernelChoice kqp{KernelChoice::kQueryPair, 16}, ki32{KernelChoice::kInt32, 16},
-        kring{KernelChoice::kPairRing, 16};
+        kring{KernelChoice::kPairRing, kRingLastR};
     s->grid = db->nsm * std::max(1, std::max({wavefront_occupancy(kqp, nullptr),
                                               wavefront_occupancy(ki32, nullptr),
                                               wavefront_occupancy(kring, nullptr)}));

@@ -520,13 +520,15 @@ __device__ __forceinline__ void ring_setup(const WavefrontArgs& a, uint8_t* smem
     __syncthreads();
 }
 
-// The pair unit of one group against one query, as process_chunk for
-// ModePairDb, with the score-profile ring instead of the int8 query profile.
+// Passes p_first .. p_first + n_pass - 1 of the pair unit of one group against one
+// query, R rows per thread, the first from query row row0 (as process_chunk for
+// ModePairDb, with the score-profile ring instead of the int8 query profile); best
+// collects the maximum.
 template <int T, int R, int S>
-__device__ __forceinline__ void process_chunk_ring(const WavefrontArgs& a, const BinArgs& bin,
-                                                   uint64_t base, uint64_t n_units,
-                                                   const ItemQuery& iq, uint8_t* smem,
-                                                   int32_t thr16) {
+__device__ __forceinline__ void ring_passes(const WavefrontArgs& a, const BinArgs& bin,
+                                            uint64_t base, uint64_t n_units, const ItemQuery& iq,
+                                            uint8_t* smem, uint32_t p_first, uint32_t n_pass,
+                                            uint32_t row0_first, uint32_t& best) {
     using Lane = LaneS16x2;
     using V = uint32_t;
     using Geo = RingGeom<T, S>;
@@ -542,7 +544,6 @@ __device__ __forceinline__ void process_chunk_ring(const WavefrontArgs& a, const
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = lane / T, t = lane % T;
     const uint32_t A = a.alphabet;
-    const uint32_t P = (iq.la + TR - 1) / TR;
     const uint64_t slot = ((uint64_t)blockIdx.x * kWarps + warp) * G + g;
     const uint64_t half = bin.bstride / 2;
     uint2* const bnd0 = bin.boundary + slot * bin.bstride;
@@ -594,14 +595,15 @@ __device__ __forceinline__ void process_chunk_ring(const WavefrontArgs& a, const
         }
     };
 
-    V best = vzero;
-    for (uint32_t p = 0; p < P; ++p) {
+    for (uint32_t p = p_first; p < p_first + n_pass; ++p) {
+        constexpr int RR = R;
+        const uint32_t row0 = row0_first + (p - p_first) * TR;
         // ring addresses of this thread's rows at the first block (slot of column -S t)
-        uint32_t cur[R];
+        uint32_t cur[RR];
         const uint32_t blk0 = (W - (uint32_t)t) & (W - 1);
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const uint32_t row = p * TR + (uint32_t)t * R + r;
+        for (int r = 0; r < RR; ++r) {
+            const uint32_t row = row0 + (uint32_t)t * RR + r;
             uint32_t c = A;
             if (row < iq.la) {
                 const uint32_t qc = iq.qa[row];
@@ -609,9 +611,9 @@ __device__ __forceinline__ void process_chunk_ring(const WavefrontArgs& a, const
             }
             cur[r] = ring_s + c * kCodeBytes + blk0 * kSlot;
         }
-        V Hl[R], Fr[R];
+        V Hl[RR], Fr[RR];
 #pragma unroll
-        for (int r = 0; r < R; ++r) { Hl[r] = vzero; Fr[r] = vzero; }
+        for (int r = 0; r < RR; ++r) { Hl[r] = vzero; Fr[r] = vzero; }
         V hb_out = vzero, eb_out = vzero, hdiag0 = vzero;  // this thread's last outputs
         V h_cur = vzero, e_cur = vzero;                     // inputs of the current step (S = 2)
         const uint2* const bnd_in = bnd0 + (p & 1) * half + S * T;
@@ -646,42 +648,44 @@ __device__ __forceinline__ void process_chunk_ring(const WavefrontArgs& a, const
                 const uint32_t* const ma = mt + (pc & 0xffu);
                 const uint32_t* const mb = mt + (pc >> 8);
                 bool dup;
-                const uint32_t at = ring_s + col_off(j, dup);
-                if constexpr (kSplit == 1) {
+                const uint32_t at0 = ring_s + col_off(j, dup);
+                // the column's word for every code at ring address `at`; the 8 columns of a
+                // block share dup, so the second copy is a branch the whole warp takes or skips
+                auto build = [&](uint32_t at) {
+                    if constexpr (kSplit == 1) {
 #pragma unroll
-                    for (int k = 0; k < 8; ++k) {
-                        if (4u * k >= A) break;
-                        const bool whole = 4u * k + 4 <= A;  // uniform: no per-code test
-                        const uint32_t wa = ma[k * kProfileRows], wb = mb[k * kProfileRows];
+                        for (int k = 0; k < 8; ++k) {
+                            if (4u * k >= A) break;
+                            const bool whole = 4u * k + 4 <= A;  // uniform: no per-code test
+                            const uint32_t wa = ma[k * kProfileRows], wb = mb[k * kProfileRows];
 #pragma unroll
-                        for (int b = 0; b < 4; ++b) {
-                            const uint32_t c = 4u * k + b;
-                            if (whole || c < A) {
-                                const uint32_t v = prmt(wa, wb, b | ((8u | b) << 4) |
-                                                                  ((4u + b) << 8) | ((12u + b) << 12));
+                            for (int b = 0; b < 4; ++b) {
+                                const uint32_t c = 4u * k + b;
+                                if (whole || c < A) {
+                                    const uint32_t v = prmt(wa, wb, b | ((8u | b) << 4) |
+                                                                      ((4u + b) << 8) | ((12u + b) << 12));
+                                    if (sw_ok(in_ring(at + c * kCodeBytes), a.dbg, 3))
+                                        sts_u32(at + c * kCodeBytes, v);
+                                }
+                            }
+                        }
+                    } else {
+                        static_assert(kSplit == 4, "codes per word");
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) {
+                            if (4u * k >= A) break;
+                            const uint32_t c = 4u * k + bq;
+                            const uint32_t wa = ma[k * kProfileRows], wb = mb[k * kProfileRows];
+                            if (c < A) {
+                                const uint32_t v = prmt(wa, wb, bsel);
                                 if (sw_ok(in_ring(at + c * kCodeBytes), a.dbg, 3))
                                     sts_u32(at + c * kCodeBytes, v);
-                                if (dup && sw_ok(in_ring(at + c * kCodeBytes + W * kSlot), a.dbg, 3))
-                                    sts_u32(at + c * kCodeBytes + W * kSlot, v);
                             }
                         }
                     }
-                } else {
-                    static_assert(kSplit == 4, "codes per word");
-#pragma unroll
-                    for (int k = 0; k < 8; ++k) {
-                        if (4u * k >= A) break;
-                        const uint32_t c = 4u * k + bq;
-                        const uint32_t wa = ma[k * kProfileRows], wb = mb[k * kProfileRows];
-                        if (c < A) {
-                            const uint32_t v = prmt(wa, wb, bsel);
-                            if (sw_ok(in_ring(at + c * kCodeBytes), a.dbg, 3))
-                                sts_u32(at + c * kCodeBytes, v);
-                            if (dup && sw_ok(in_ring(at + c * kCodeBytes + W * kSlot), a.dbg, 3))
-                                sts_u32(at + c * kCodeBytes + W * kSlot, v);
-                        }
-                    }
-                }
+                };
+                build(at0);
+                if (dup) build(at0 + W * kSlot);
             }
             if (s0 == 0 && t + 1 < T) {
                 // columns -S(T-1) .. -1 score 0 at the start of a pass: slots W-T+1 .. W-1
@@ -728,36 +732,83 @@ __device__ __forceinline__ void process_chunk_ring(const WavefrontArgs& a, const
                     e_cur = e_nxt;
                 }
                 const uint32_t koff = S == 1 ? k * kSlot : (k & 1) * Geo::kPlane + (k >> 1) * kSlot;
-                V diag = hdiag0;
-                V E = e_in;
+                // x = H[i-1][j-1] + fsbt of every row first (last row first, in place: the
+                // row below has used the old H by then), then the H, E, F chain down the rows
 #pragma unroll
-                for (int r = 0; r < R; ++r) {
+                for (int r = RR - 1; r >= 0; --r) {
                     V sc = 0;
                     if (sw_ok(in_ring(cur[r] + koff), a.dbg, 2)) sc = lds_u32(cur[r] + koff);
-                    const V x = Lane::vadd(diag, sc);              // H[i-1][j-1] + fsbt
+                    Hl[r] = Lane::vadd(r > 0 ? Hl[r - 1] : hdiag0, sc);
+                }
+                V E = e_in;
+#pragma unroll
+                for (int r = 0; r < RR; ++r) {
+                    const V x = Hl[r];
                     const V H = Lane::max3_relu(x, E, Fr[r]);      // H[i][j]
-                    diag = Hl[r];
                     Hl[r] = H;
                     const V hb = Lane::vadd(H, vbeta);             // H[i][j] - beta
                     E = Lane::addmax(E, valpha, hb);               // E[i+1][j]
                     Fr[r] = Lane::addmax(Fr[r], valpha, hb);       // F[i][j+1]
                     best = Lane::vmax(best, x);                    // max H = max(0, max x)
                 }
-                hb_out = Hl[R - 1];
+                hb_out = Hl[RR - 1];
                 eb_out = E;
                 hdiag0 = h_in;
+                // two 32-bit stores: measured faster than one 64-bit store with 32 lanes per
+                // group, and no slower with 8
                 if (t == T - 1 && sw_ok((int64_t)(S * T) + (int64_t)(s0 + k) - S * (T - 1) >= 0 &&
                                             (uint64_t)(S * T + s0 + k - S * (T - 1)) < half,
-                                        a.dbg, 7))
-                    bo[k] = make_uint2((uint32_t)hb_out, (uint32_t)eb_out);
+                                        a.dbg, 7)) {
+                    bo[k].x = (uint32_t)hb_out;
+                    bo[k].y = (uint32_t)eb_out;
+                }
             }
             // next block: slots advance by kAdvance, wrapping at W
             const uint32_t blk = ((s0 / S) - (uint32_t)t) & (W - 1);
             const uint32_t delta = (blk + kAdvance < W ? kAdvance : kAdvance - W) * kSlot;
 #pragma unroll
-            for (int r = 0; r < R; ++r) cur[r] += delta;
+            for (int r = 0; r < RR; ++r) cur[r] += delta;
         }
     }
+}
+
+// The last pass of fewer rows, compiled apart from the caller so that the whole-pass
+// loop keeps its own register allocation and schedule.
+template <int T, int R, int S>
+__device__ __noinline__ void ring_last_pass(const WavefrontArgs& a, const BinArgs& bin,
+                                            uint64_t base, uint64_t n_units, const ItemQuery& iq,
+                                            uint8_t* smem, uint32_t p, uint32_t row0,
+                                            uint32_t& best) {
+    ring_passes<T, R, S>(a, bin, base, n_units, iq, smem, p, 1, row0, best);
+}
+
+// The pair unit of one group against one query in passes of T R rows; with 8 threads
+// of 24 rows, the rows left after the whole passes take one pass of 8, 16 or 24 rows per
+// thread (ring_last_rows: fewer padded rows).
+template <int T, int R, int S>
+__device__ __forceinline__ void process_chunk_ring(const WavefrontArgs& a, const BinArgs& bin,
+                                                   uint64_t base, uint64_t n_units,
+                                                   const ItemQuery& iq, uint8_t* smem,
+                                                   int32_t thr16) {
+    using Lane = LaneS16x2;
+    using V = uint32_t;
+    constexpr uint32_t TR = T * R;
+    constexpr bool kShortLast = T == kShortT && R == kRingLastR;
+    const uint32_t P = kShortLast ? iq.la / TR : (iq.la + TR - 1) / TR;
+    const int last = kShortLast ? ring_last_rows(iq.la - P * TR) : 0;
+    V best = 0;
+    ring_passes<T, R, S>(a, bin, base, n_units, iq, smem, 0, P + (last == R), 0, best);
+    if constexpr (kShortLast) {
+        if (last == 8)
+            ring_last_pass<T, 8, S>(a, bin, base, n_units, iq, smem, P, P * TR, best);
+        else if (last == 16)
+            ring_last_pass<T, 16, S>(a, bin, base, n_units, iq, smem, P, P * TR, best);
+    }
+    const int lane = threadIdx.x & 31;
+    const int t = lane % T;
+    const uint64_t u = base + (uint64_t)(threadIdx.x >> 5) * (32 / T) + lane / T;
+    const bool have = u < n_units;
+    const uint64_t sp = 2 * (bin.first_unit + u);
 
     // ---- group maximum and results ----
 #pragma unroll
