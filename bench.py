@@ -80,8 +80,9 @@ def parse_args():
     p.add_argument("--batch-seqs", type=int, default=1_000_000)
     p.add_argument("--batch-queries", type=int, default=256)
     p.add_argument("--serve-seqs", type=int, default=20_000_000)
-    p.add_argument("--serve-rates", default="1.0",
-                   help="comma-separated Poisson arrival rates (queries/s); empty skips serving")
+    p.add_argument("--serve-rates", default="1.0,10",
+                   help="comma-separated Poisson arrival rates (queries/s; 10 and above are past "
+                        "one GPU's capacity); empty skips serving")
     p.add_argument("--serve-arrivals", type=int, default=16)
     p.add_argument("--long-steps", type=int, default=2,
                    help="timed searches of the long-sequence workloads (config 4 and 4b; 0 skips)")
