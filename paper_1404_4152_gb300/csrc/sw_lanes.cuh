@@ -53,5 +53,31 @@ struct LaneS32 {
     static __device__ __forceinline__ V max3_relu(V a, V b, V c) { return __vimax3_s32_relu(a, b, c); }
 };
 
+// Shared-memory accesses by byte address (the state space known, no generic-address
+// conversion).
+static __device__ __forceinline__ uint32_t lds_u32(uint32_t addr) {
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr));
+    return v;
+}
+// The value of the thread above (shfl.up within segments of T threads); the
+// first thread of a segment, which has none, loads it from shared memory.
+template <int T>
+static __device__ __forceinline__ uint32_t shfl_up_or_lds(uint32_t v, uint32_t addr) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "shfl.sync.up.b32 %0|p, %1, 1, %3, -1;\n\t"
+        "@!p ld.shared.u32 %0, [%2];\n\t}"
+        : "=r"(r)
+        : "r"(v), "r"(addr), "n"((32 - T) << 8));
+    return r;
+}
+static __device__ __forceinline__ void sts_u32(uint32_t addr, uint32_t v) {
+    asm volatile("st.shared.u32 [%0], %1;" ::"r"(addr), "r"(v));
+}
+static __device__ __forceinline__ void sts_u64(uint32_t addr, uint2 v) {
+    asm volatile("st.shared.v2.u32 [%0], {%1, %2};" ::"r"(addr), "r"(v.x), "r"(v.y));
+}
 
 }  // namespace swgb

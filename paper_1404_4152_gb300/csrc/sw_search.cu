@@ -30,7 +30,6 @@ using namespace swgb;
 namespace {
 
 constexpr int kTopkBlocks = 256;
-constexpr int kRescoreBlocksPerSm = 4;
 constexpr uint64_t kRescoreScratch = 256ull << 20;
 
 const int kShortR[] = {8, 12, 16, 20, 24};
@@ -197,14 +196,15 @@ sw_status sw_db_prepare_search(sw_db* db) {
                            "boundary rows (long)")))
             return st;
     }
-    // rescoring: one block per pair, up to kRescoreBlocksPerSm per SM, each with one
-    // scratch row (bstride entries), as many as kRescoreScratch bytes allow
+    // rescoring: one block per pair, as many per SM as fit (its score rings take most of
+    // the shared memory), each with one scratch row (bstride entries), as many as
+    // kRescoreScratch bytes allow
     db->bstride_rescore = bstride_for(std::max(4u, (db->max_len + 3u) & ~3u));
     {
         const uint64_t per_block = db->bstride_rescore * sizeof(uint2);
         const uint64_t fit = ((uint64_t)kRescoreScratch) / std::max<uint64_t>(per_block, 1);
         db->grid_rescore = (int)std::max<uint64_t>(
-            1, std::min<uint64_t>(fit, (uint64_t)db->nsm * kRescoreBlocksPerSm));
+            1, std::min<uint64_t>(fit, (uint64_t)db->nsm * rescore_blocks_per_sm(db->alphabet)));
     }
     if ((st = db_alloc(db, (void**)&db->d_bnd_rescore,
                        (uint64_t)db->grid_rescore * db->bstride_rescore * sizeof(uint2),

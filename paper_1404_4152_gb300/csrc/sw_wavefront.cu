@@ -478,31 +478,6 @@ __host__ __device__ constexpr size_t ring_smem_bytes(uint32_t alphabet, int S) {
     return kRingOffset + (size_t)kWarps * (alphabet + 1) * (S == 1 ? ring_row_words<1>() : ring_row_words<2>()) * 4;
 }
 
-__device__ __forceinline__ uint32_t lds_u32(uint32_t addr) {
-    uint32_t v;
-    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr));
-    return v;
-}
-// The value of the thread above (shfl.up within segments of T threads); the
-// first thread of a segment, which has none, loads it from shared memory.
-template <int T>
-__device__ __forceinline__ uint32_t shfl_up_or_lds(uint32_t v, uint32_t addr) {
-    uint32_t r;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "shfl.sync.up.b32 %0|p, %1, 1, %3, -1;\n\t"
-        "@!p ld.shared.u32 %0, [%2];\n\t}"
-        : "=r"(r)
-        : "r"(v), "r"(addr), "n"((32 - T) << 8));
-    return r;
-}
-__device__ __forceinline__ void sts_u32(uint32_t addr, uint32_t v) {
-    asm volatile("st.shared.u32 [%0], %1;" ::"r"(addr), "r"(v));
-}
-__device__ __forceinline__ void sts_u64(uint32_t addr, uint2 v) {
-    asm volatile("st.shared.v2.u32 [%0], {%1, %2};" ::"r"(addr), "r"(v.x), "r"(v.y));
-}
-
 // Once per block: the matrix by database code, and every warp's all-zero row.
 template <int S>
 __device__ __forceinline__ void ring_setup(const WavefrontArgs& a, uint8_t* smem) {

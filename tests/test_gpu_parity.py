@@ -261,3 +261,45 @@ def test_two_handles_from_two_threads():
     for key, v in alone.items():
         assert np.array_equal(got[key], v), key
     assert np.array_equal(alone[("a", 1)], oracle.scores(qs[1], ra, oa, synth.BLOSUM62, 1, 11))
+
+
+@pytest.mark.parametrize("A", [20, 32])
+def test_rescoring_bands_rounds_and_lengths(A, kflags):
+    """Saturated pairs of many shapes go through the int32 rescoring kernel: a query of
+    2,600 rows (11 bands of 256 rows, so two rounds of the 8 warps, handing rows on through
+    the global scratch row), planted sequences shorter and longer than 16 column blocks of
+    64, lengths that are not multiples of 64, a local match inside random flanks, one above
+    the long-sequence threshold; every score must equal the oracle's."""
+    rng = np.random.default_rng(71 + A)
+    qlen = 2600
+    q = rng.integers(0, A, size=qlen).astype(np.uint8)
+    # a matrix with a strong diagonal: near-copies of the query pass the 16-bit range
+    M = rng.integers(-6, 4, size=(A, A)).astype(np.int8)
+    np.fill_diagonal(M, 60)
+    lengths = synth.gen_lengths(300, synth.db_qtable(), 72, 1)
+    res, off = _db_from_lengths(lengths, 72, A)
+    seqs = [res[int(off[i]):int(off[i + 1])] for i in range(len(lengths))]
+
+    def mutated(x, rate):
+        y = x.copy()
+        hit = rng.random(y.size) < rate
+        y[hit] = rng.integers(0, A, size=int(hit.sum()))
+        return y
+
+    planted = {
+        5: mutated(q, 0.05),                                   # whole query, L = 2600
+        40: mutated(q[:700], 0.03),                            # 700 columns (< 16 blocks)
+        41: mutated(q[1000:1999], 0.03),                       # 999 columns
+        90: np.concatenate([rng.integers(0, A, 450).astype(np.uint8), mutated(q[300:1500], 0.04),
+                            rng.integers(0, A, 777).astype(np.uint8)]),   # local, in flanks
+        150: np.concatenate([mutated(q, 0.02), rng.integers(0, A, 900).astype(np.uint8)]),
+        299: mutated(q[::-1][:1300], 0.0),                     # reversed: no long match
+    }
+    for p, s in planted.items():
+        seqs[p] = s
+    res = np.concatenate(seqs)
+    off = np.zeros(len(seqs) + 1, np.uint64)
+    off[1:] = np.cumsum([s.size for s in seqs])
+    with sw.sw_db_load(res, off, alphabet=A, long_threshold=3000, flags=kflags) as db:
+        scores, stats = _check(db, res, off, q, M, 3, 20, 10, expect_recompute=True)
+    assert stats["recomputed"] >= 4 and scores.max() > 32767
