@@ -4,8 +4,9 @@
 // future work; a database search reports them for its top hits. Three
 // dynamic programmes per (query, sequence) pair, in int32, each a lane
 // wavefront of one warp (lane t on column s - t at step s, kR query rows per
-// lane, passes of 32 kR rows with the bottom row kept in the warp's scratch;
-// a block is one warp, so the hits spread over every SM):
+// lane, passes of 32 kR rows with the bottom row kept in the warp's scratch,
+// scores from the warp's score ring; a block is one warp, so the hits spread
+// over every SM):
 //
 //  1. recurrence (1) with the score S and the end cell: the first (i, j), in
 //     order of i then j, whose H equals S;
@@ -32,6 +33,7 @@
 #include "sw.h"
 #include "sw_db.h"
 #include "sw_internal.h"
+#include "sw_lanes.cuh"
 
 namespace swgb {
 
@@ -78,35 +80,66 @@ struct AlignArgs {
 
 __device__ __forceinline__ int32_t imax(int32_t a, int32_t b) { return a > b ? a : b; }
 
+// The warp's score ring (the score profile of Section III.B.2 over a window of
+// columns): word [c][j mod kW] = fsbt(c, d_j) for every query code c and the columns a
+// 32-step block touches (its 32 and the 31 the lane skew reaches back); slots below kD
+// are also kept at kW + slot so a sub-block of 8 steps reads 8 consecutive slots from one
+// base. Code rows are kRowWords apart (a multiple of 32) and the 32 lanes read 32
+// consecutive columns, so the loads are conflict-free. Row A is zero (rows past the query).
+constexpr uint32_t kW = 64;
+constexpr uint32_t kD = 8;
+constexpr uint32_t kRowWords = 96;
+static_assert(kW >= 2 * kT - 1 && kW + kD <= kRowWords && kRowWords % 32 == 0 && kW % 32 == 0,
+              "score ring");
+
+struct WarpSmem {
+    uint32_t ring[kM * kRowWords];  // (A + 1) code rows used
+    uint2 stage[kT];                // lane 0's top entries of the current block
+};
+
 // One dynamic programme over rows x cols by one warp. MODE 0: recurrence (1),
 // tracking the first maximal cell; MODE 1: anchored at (0, 0), tracking the first
 // cell whose aligned-pair value is S; MODE 2: anchored at (0, 0), writing each
 // cell's traceback byte to dir[row * cols + col].
 template <int MODE, class QF, class DF>
-__device__ void run_dp(const AlignArgs& a, const int32_t* sM, uint2* bnd0, uint64_t half, int t,
-                       uint32_t rows, uint32_t cols, QF qf, DF df, int32_t S, int32_t& best,
-                       uint32_t& bi, uint32_t& bj, uint8_t* dir) {
+__device__ void run_dp(const AlignArgs& a, const int32_t* sM, WarpSmem& ws, uint2* bnd0,
+                       uint64_t half, int t, uint32_t rows, uint32_t cols, QF qf, DF df, int32_t S,
+                       int32_t& best, uint32_t& bi, uint32_t& bj, uint8_t* dir) {
     const int32_t border = MODE == 0 ? 0 : kNeg;
+    const uint32_t A = a.alphabet;
     const uint32_t P = (rows + kRows - 1) / kRows;
     const uint32_t steps = cols + kT - 1;
+    const uint32_t ring_s = (uint32_t)__cvta_generic_to_shared(ws.ring);
+    const uint32_t stage_s = (uint32_t)__cvta_generic_to_shared(ws.stage);
+    const uint32_t ring_hi = ring_s + (A + 1) * kRowWords * 4;
+    auto in_ring = [&](uint32_t addr) { return addr >= ring_s && addr + 4 <= ring_hi; };
     for (uint32_t p = 0; p < P; ++p) {
-        uint32_t qc[kR];
+        // score-ring address of each of this lane's rows at the slot of column -t
+        uint32_t addr[kR];
+        const uint32_t sl0 = (kW - (uint32_t)t) % kW;
 #pragma unroll
         for (int r = 0; r < kR; ++r) {
             const uint32_t row = p * kRows + (uint32_t)t * kR + r;
-            uint32_t c = row < rows ? qf(row) : kPadCode;
-            qc[r] = (c < a.alphabet ? c : kPadCode) * kM;
+            uint32_t c = row < rows ? qf(row) : A;
+            if (c > A) c = A;
+            addr[r] = ring_s + (c * kRowWords + sl0) * 4;
+        }
+        __syncwarp();  // the previous pass has finished reading the ring
+        // columns -31 .. -1 score 0 (slots kW - 31 .. kW - 1)
+        for (uint32_t i = t; i < A * (kT - 1); i += kT) {
+            const uint32_t at = ring_s + ((i / (kT - 1)) * kRowWords + kW - (kT - 1) + i % (kT - 1)) * 4;
+            if (sw_ok(in_ring(at), a.dbg, 26)) sts_u32(at, 0u);
         }
         int32_t Hl[kR], Fr[kR];
         uint32_t fx = 0;  // MODE 2: extension bit of Fr[r] in bit r
 #pragma unroll
         for (int r = 0; r < kR; ++r) { Hl[r] = border; Fr[r] = border; }
         int32_t hb_out = border, eb_out = border, hdiag0 = border;
-        uint32_t code_out = kPadCode, ex_out = 0;
+        uint32_t ex_out = 0;
         const uint2* bin = bnd0 + (p & 1) * half + kT;
         uint2* bout = bnd0 + ((p + 1) & 1) * half + kT;
-        // lane t holds the code and top-row entry of column s0 + t for the current block of
-        // 32 steps and of the next one; lane 0 takes them with a shuffle
+        // lane t builds column s0 + t of each block of 32 steps and stages its top-row entry;
+        // its code and entry are loaded one block ahead
         auto code_at = [&](uint32_t j) -> uint32_t {
             uint32_t c = j < cols ? df(j) : kPadCode;
             return c > kPadCode ? kPadCode : c;
@@ -116,89 +149,100 @@ __device__ void run_dp(const AlignArgs& a, const int32_t* sM, uint2* bnd0, uint6
         auto top_at = [&](uint32_t j) -> uint2 {
             return (p > 0 && j < cols && sw_ok(kT + (uint64_t)j < half, a.dbg, 22)) ? bin[j] : kBorder;
         };
-        uint32_t cblk = code_at(t), cnext = code_at(32 + t);
-        uint2 tblk = top_at(t), tnext = top_at(32 + t);
-        for (uint32_t s = 0; s < steps; ++s) {
-            const uint32_t k = s & 31u;
-            if (k == 0 && s > 0) {
-                cblk = cnext;
-                tblk = tnext;
-                cnext = code_at(s + 32 + t);
-                tnext = top_at(s + 32 + t);
-            }
-            const uint32_t c0 = __shfl_sync(0xffffffffu, cblk, k);
-            const uint32_t t0x = __shfl_sync(0xffffffffu, tblk.x, k);
-            const uint32_t t0y = __shfl_sync(0xffffffffu, tblk.y, k);
-            int32_t h_in = (int32_t)__shfl_up_sync(0xffffffffu, (uint32_t)hb_out, 1);
-            int32_t e_in = (int32_t)__shfl_up_sync(0xffffffffu, (uint32_t)eb_out, 1);
-            uint32_t code = __shfl_up_sync(0xffffffffu, code_out, 1);
-            uint32_t ex = __shfl_up_sync(0xffffffffu, ex_out, 1);
-            if (t == 0) {
-                code = c0;
-                h_in = (int32_t)t0x;
-                e_in = MODE == 2 ? ((int32_t)t0y >> 1) : (int32_t)t0y;
-                ex = MODE == 2 ? (t0y & 1u) : 0u;
-            }
-            code_out = code;
-            const int64_t j = (int64_t)s - t;
-            int32_t diag = hdiag0, E = e_in;
-#pragma unroll
-            for (int r = 0; r < kR; ++r) {
-                const uint32_t i = p * kRows + (uint32_t)t * kR + r;
-                const bool valid = i < rows && j >= 0 && j < (int64_t)cols;
-                const int32_t sc = sM[qc[r] + code];
-                int32_t H, En, Fn;
-                if (MODE == 0) {
-                    H = imax(imax(diag + sc, 0), imax(E, Fr[r]));
-                    if (valid && (H > best || (H == best && (i < bi || (i == bi && (uint32_t)j < bj))))) {
-                        best = H;
-                        bi = i;
-                        bj = (uint32_t)j;
-                    }
-                    const int32_t hb = H - a.beta;
-                    En = imax(E - a.alpha, hb);
-                    Fn = imax(Fr[r] - a.alpha, hb);
-                } else {
-                    const int32_t Mv = (i == 0 && j == 0) ? sc : imax(diag + sc, kNeg);
-                    const int32_t F = Fr[r];
-                    H = imax(Mv, imax(E, F));
-                    if (MODE == 1) {
-                        if (valid && Mv == S && (i < bi || (i == bi && (uint32_t)j < bj))) {
-                            bi = i;
-                            bj = (uint32_t)j;
-                        }
-                    } else if (valid && sw_ok((uint64_t)i * cols + (uint64_t)j < (uint64_t)rows * cols,
-                                              a.dbg, 21)) {
-                        const uint32_t hsel = (Mv >= E && Mv >= F) ? 0u : (E >= F ? 1u : 2u);
-                        dir[(uint64_t)i * cols + (uint64_t)j] =
-                            (uint8_t)(hsel | (ex << 2) | (((fx >> r) & 1u) << 3));
-                    }
-                    const int32_t hb = H - a.beta;
-                    const uint32_t exn = (E - a.alpha >= hb) ? 1u : 0u;
-                    const uint32_t fxn = (F - a.alpha >= hb) ? 1u : 0u;
-                    En = imax(imax(E - a.alpha, hb), kNeg);
-                    Fn = imax(imax(F - a.alpha, hb), kNeg);
-                    if (!valid) {
-                        H = kNeg;
-                        En = kNeg;
-                        Fn = kNeg;
-                    }
-                    ex = valid ? exn : 0u;
-                    if (MODE == 2) fx = (fx & ~(1u << r)) | ((valid ? fxn : 0u) << r);
+        uint32_t cnext = code_at(t);
+        uint2 tnext = top_at(t);
+        for (uint32_t s0 = 0; s0 < steps; s0 += kT) {
+            __syncwarp();  // the previous block has finished with the slots and the stage
+            {
+                const uint32_t j = s0 + (uint32_t)t, d = cnext, sl = j % kW;
+                for (uint32_t c = 0; c < A; ++c) {
+                    const uint32_t at = ring_s + (c * kRowWords + sl) * 4;
+                    const uint32_t v = (uint32_t)sM[c * kM + d];
+                    if (sw_ok(in_ring(at), a.dbg, 26)) sts_u32(at, v);
+                    if (sl < kD && sw_ok(in_ring(at + kW * 4), a.dbg, 26)) sts_u32(at + kW * 4, v);
                 }
-                diag = Hl[r];
-                Hl[r] = H;
-                E = En;
-                Fr[r] = Fn;
+                ws.stage[t] = tnext;
+                cnext = code_at(j + kT);
+                tnext = top_at(j + kT);
             }
-            hb_out = Hl[kR - 1];
-            eb_out = E;
-            ex_out = ex;
-            hdiag0 = h_in;
-            if (t == kT - 1 && p + 1 < P && j >= 0 && j < (int64_t)cols &&
-                sw_ok(kT + (uint64_t)j < half, a.dbg, 23)) {
-                const uint32_t ev = MODE == 2 ? ((uint32_t)eb_out << 1) | ex_out : (uint32_t)eb_out;
-                bout[j] = make_uint2((uint32_t)hb_out, ev);
+            __syncwarp();  // this block's columns and top entries are visible
+            for (uint32_t sb = 0; sb < (uint32_t)kT && s0 + sb < steps; sb += 8) {
+                const uint32_t st_sb = stage_s + sb * 8;
+#pragma unroll
+                for (int k8 = 0; k8 < 8; ++k8) {
+                    const uint32_t s = s0 + sb + (uint32_t)k8;
+                    const int32_t h_in = (int32_t)shfl_up_or_lds<kT>((uint32_t)hb_out, st_sb + k8 * 8);
+                    const uint32_t pk = shfl_up_or_lds<kT>(
+                        MODE == 2 ? ((uint32_t)eb_out << 1) | ex_out : (uint32_t)eb_out, st_sb + k8 * 8 + 4);
+                    const int32_t e_in = MODE == 2 ? ((int32_t)pk >> 1) : (int32_t)pk;
+                    uint32_t ex = MODE == 2 ? (pk & 1u) : 0u;
+                    const int64_t j = (int64_t)s - t;
+                    int32_t diag = hdiag0, E = e_in;
+#pragma unroll
+                    for (int r = 0; r < kR; ++r) {
+                        const uint32_t i = p * kRows + (uint32_t)t * kR + r;
+                        const bool valid = i < rows && j >= 0 && j < (int64_t)cols;
+                        int32_t sc = 0;
+                        if (sw_ok(in_ring(addr[r] + k8 * 4), a.dbg, 26)) sc = (int32_t)lds_u32(addr[r] + k8 * 4);
+                        int32_t H, En, Fn;
+                        if (MODE == 0) {
+                            H = imax(imax(diag + sc, 0), imax(E, Fr[r]));
+                            if (valid && (H > best || (H == best && (i < bi || (i == bi && (uint32_t)j < bj))))) {
+                                best = H;
+                                bi = i;
+                                bj = (uint32_t)j;
+                            }
+                            const int32_t hb = H - a.beta;
+                            En = imax(E - a.alpha, hb);
+                            Fn = imax(Fr[r] - a.alpha, hb);
+                        } else {
+                            const int32_t Mv = (i == 0 && j == 0) ? sc : imax(diag + sc, kNeg);
+                            const int32_t F = Fr[r];
+                            H = imax(Mv, imax(E, F));
+                            if (MODE == 1) {
+                                if (valid && Mv == S && (i < bi || (i == bi && (uint32_t)j < bj))) {
+                                    bi = i;
+                                    bj = (uint32_t)j;
+                                }
+                            } else if (valid && sw_ok((uint64_t)i * cols + (uint64_t)j < (uint64_t)rows * cols,
+                                                      a.dbg, 21)) {
+                                const uint32_t hsel = (Mv >= E && Mv >= F) ? 0u : (E >= F ? 1u : 2u);
+                                dir[(uint64_t)i * cols + (uint64_t)j] =
+                                    (uint8_t)(hsel | (ex << 2) | (((fx >> r) & 1u) << 3));
+                            }
+                            const int32_t hb = H - a.beta;
+                            const uint32_t exn = (E - a.alpha >= hb) ? 1u : 0u;
+                            const uint32_t fxn = (F - a.alpha >= hb) ? 1u : 0u;
+                            En = imax(imax(E - a.alpha, hb), kNeg);
+                            Fn = imax(imax(F - a.alpha, hb), kNeg);
+                            if (!valid) {
+                                H = kNeg;
+                                En = kNeg;
+                                Fn = kNeg;
+                            }
+                            ex = valid ? exn : 0u;
+                            if (MODE == 2) fx = (fx & ~(1u << r)) | ((valid ? fxn : 0u) << r);
+                        }
+                        diag = Hl[r];
+                        Hl[r] = H;
+                        E = En;
+                        Fr[r] = Fn;
+                    }
+                    hb_out = Hl[kR - 1];
+                    eb_out = E;
+                    ex_out = ex;
+                    hdiag0 = h_in;
+                    if (t == kT - 1 && p + 1 < P && j >= 0 && j < (int64_t)cols &&
+                        sw_ok(kT + (uint64_t)j < half, a.dbg, 23)) {
+                        const uint32_t ev = MODE == 2 ? ((uint32_t)eb_out << 1) | ex_out : (uint32_t)eb_out;
+                        bout[j] = make_uint2((uint32_t)hb_out, ev);
+                    }
+                }
+                // next sub-block: 8 slots on, wrapping at kW (the lane's slot is kW - t + s)
+                const uint32_t sl = (s0 + sb + kW - (uint32_t)t) % kW;
+                const uint32_t delta = (sl + 8 < kW ? 8u : 8u - kW) * 4u;
+#pragma unroll
+                for (int r = 0; r < kR; ++r) addr[r] += delta;
             }
         }
     }
@@ -206,6 +250,7 @@ __device__ void run_dp(const AlignArgs& a, const int32_t* sM, uint2* bnd0, uint6
 
 __global__ void __launch_bounds__(kThreads) align_kernel(const AlignArgs a) {
     __shared__ int32_t sM[kM * kM];
+    __shared__ WarpSmem wsm[kWarps];
     for (uint32_t i = threadIdx.x; i < kM * kM; i += kThreads) {
         const uint32_t r = i / kM, c = i % kM;
         sM[i] = (r < a.alphabet && c < a.alphabet) ? (int32_t)a.matrix[r * a.alphabet + c] : 0;
@@ -232,7 +277,7 @@ __global__ void __launch_bounds__(kThreads) align_kernel(const AlignArgs a) {
             int32_t best = 0;
             uint32_t bi = 0xffffffffu, bj = 0xffffffffu;
             if (qlen && n)
-                run_dp<0>(a, sM, bnd0, half, t, qlen, n, [q](uint32_t i) -> uint32_t { return q[i]; },
+                run_dp<0>(a, sM, wsm[w], bnd0, half, t, qlen, n, [q](uint32_t i) -> uint32_t { return q[i]; },
                           dcode, 0, best, bi, bj, nullptr);
             // first maximal cell over the warp
 #pragma unroll
@@ -251,7 +296,7 @@ __global__ void __launch_bounds__(kThreads) align_kernel(const AlignArgs a) {
                 const uint32_t ie = bi, je = bj;
                 int32_t unused = 0;
                 uint32_t ui = 0xffffffffu, uj = 0xffffffffu;
-                run_dp<1>(a, sM, bnd0, half, t, ie + 1, je + 1,
+                run_dp<1>(a, sM, wsm[w], bnd0, half, t, ie + 1, je + 1,
                           [q, ie](uint32_t u) -> uint32_t { return q[ie - u]; },
                           [dcode, je](uint32_t v) -> uint32_t { return dcode(je - v); }, best, unused,
                           ui, uj, nullptr);
@@ -289,7 +334,7 @@ __global__ void __launch_bounds__(kThreads) align_kernel(const AlignArgs a) {
             uint8_t* dir = a.dir + hit.dir_off;
             int32_t unused = 0;
             uint32_t ui = 0, uj = 0;
-            run_dp<2>(a, sM, bnd0, half, t, rows, cols,
+            run_dp<2>(a, sM, wsm[w], bnd0, half, t, rows, cols,
                       [q, is](uint32_t u) -> uint32_t { return q[is + u]; },
                       [dcode, js](uint32_t v) -> uint32_t { return dcode(js + v); }, hit.score,
                       unused, ui, uj, dir);
