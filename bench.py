@@ -57,7 +57,7 @@ PAPER_PHI_GCUPS_MAX = 58.8    # SWAPHI InterSP, one Xeon Phi 5110P, TrEMBL (Sect
 # profiles/search_kernel_ring_807x600k_ncu.md), valid for the kernel source whose sha256
 # starts with TRAFFIC_SOURCE.
 TRAFFIC_BYTES_PER_CELL = 0.0187
-TRAFFIC_SOURCE = "5481cce112a758ca"
+TRAFFIC_SOURCE = "ed66652d0f60ff7b"
 # ALU instructions per row update of that kernel in the same capture (ALU-pipe instructions
 # over row updates: VIADDMNMX, VIMNMX3, PRMT, ISETP, LOP3, ...; the 807-row query's last
 # pass of 8 rows per thread included): the mix the kernel executes, against the 3.5 minimum
