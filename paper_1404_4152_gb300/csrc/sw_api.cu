@@ -108,6 +108,9 @@ void release(sw_db* db) {
     for (auto& a : db->allocs) db_free(db, a.first, a.second);
     db->allocs.clear();
     if (db->stream) cudaStreamDestroy(db->stream);
+    if (db->a_stream) cudaStreamDestroy(db->a_stream);
+    if (db->a_ev0) cudaEventDestroy(db->a_ev0);
+    if (db->a_ev1) cudaEventDestroy(db->a_ev1);
     if (db->ev_t0) cudaEventDestroy(db->ev_t0);
     if (db->ev_t1) cudaEventDestroy(db->ev_t1);
     if (db->h_pinned) cudaFreeHost(db->h_pinned);

@@ -95,6 +95,8 @@ struct sw_db {
     // batch buffers (grown on demand) and the captured batch graph
     DevBuf b_pairs, b_qoff, b_qlen, b_flags, b_topk, b_queries, b_scores, b_top;
     DevBuf a_rows, a_hits, a_dir, a_ops;  // sw_align scratch (grow-only)
+    cudaStream_t a_stream = nullptr;      // sw_align: the long hits' kernel beside the others
+    cudaEvent_t a_ev0 = nullptr, a_ev1 = nullptr;
     BatchGraph graph;
 
     // autotuning (sw_db_autotune)

@@ -103,3 +103,32 @@ def test_batch_of_queries_matches_single_calls():
         e = oracle.align(qs[i], w.residues[int(w.offsets[x]):int(w.offsets[x + 1])], w.matrix,
                          w.alpha, w.beta)
         assert all(g[k] == e[k] for k in e)
+
+
+@pytest.mark.parametrize("ab", [(1, 11), (5, 2), (0, 5)])
+def test_long_hits_in_the_block_kernel(ab):
+    """Hits of at least 2^21 cells take the score and start-cell programmes in the
+    8-warp block kernel (bands of 256 rows, two rounds of warps for a 2,600-row query),
+    beside short hits in the one-warp kernel; every alignment must match the oracle's
+    letter for letter."""
+    alpha, beta = ab
+    rng = np.random.default_rng(31 + alpha)
+    q = synth.make_queries([2600], 32 + alpha)[0]
+    flank = lambda n: synth.make_queries([n], int(rng.integers(1, 1 << 30)))[0]
+    seqs = [
+        synth.mutate(q, 33, 1, 0, 500),                                  # 2600 x 2600
+        np.concatenate([flank(700), synth.mutate(q[200:1900], 33, 2, 1, 700), flank(900)]),
+        np.concatenate([flank(3000), q[2100:2600]]),                     # match at the ends
+        q[::-1].copy(),                                                  # no long match
+        synth.mutate(q[:1000], 33, 3, 2, 300),                           # 2.6 M cells
+        flank(820),                                                      # 2.1 M: random
+        flank(300),                                                      # short hits too
+        synth.mutate(q[1200:1500], 33, 4, 3, 400),
+    ]
+    res = np.concatenate(seqs)
+    off = np.zeros(len(seqs) + 1, np.uint64)
+    off[1:] = np.cumsum([s.size for s in seqs])
+    with sw.sw_db_load(res, off) as db:
+        got = _check(db, res, off, q, synth.BLOSUM62, alpha, beta,
+                     np.arange(len(seqs), dtype=np.uint64))
+    assert got[0]["score"] > 0 and len(got[0]["ops"]) > 2000
