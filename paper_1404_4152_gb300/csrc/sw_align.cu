@@ -35,6 +35,7 @@
 #include <vector>
 
 #include "sw.h"
+#include "sw_blockwave.cuh"
 #include "sw_db.h"
 #include "sw_internal.h"
 #include "sw_lanes.cuh"
@@ -51,7 +52,9 @@ constexpr int kR = 12;
 constexpr int kRows = kT * kR;
 constexpr int kM = kProfileRows;
 constexpr int32_t kNeg = -(1 << 29);  // minus infinity for the anchored programmes
-constexpr uint64_t kLongCells = 1ull << 21;  // hits of this many cells go to the block kernel
+// hits of this many cells go to the block kernel (measured on the top hits of config 1:
+// 2^20 4.9 ms per batch, 2^21 7.1 ms, 2^22 11.6 ms)
+constexpr uint64_t kLongCells = 1ull << 20;
 
 struct AlignHit {
     uint64_t sp;        // sorted position of the sequence
@@ -259,235 +262,13 @@ __device__ void run_dp(const AlignArgs& a, const int32_t* sM, WarpSmem& ws, uint
 
 // ---------------------------------------------------------------------------
 // Long hits: programmes 1 and 2 by a block of 8 warps (the wavefront of warps over
-// bands of query rows of the rescoring kernel), so the longest hits of a batch do not
+// bands of query rows of sw_blockwave.cuh), so the longest hits of a batch do not
 // leave one warp working long after the rest of the GPU is done.
 // ---------------------------------------------------------------------------
-constexpr int kBWarps = 8;
-constexpr int kBThreads = kBWarps * 32;
-constexpr int kBR = 8;                  // rows per lane
-constexpr int kBBand = kT * kBR;        // rows per band
-constexpr int kBC = 64;                 // lane-steps per super-step
-constexpr int kBRing = 4 * kBC;         // bottom-row entries kept per warp
-constexpr int kBLag = 2;                // blocks between consecutive warps
-constexpr int kBMinNBP = 16;            // > kBLag * (kBWarps - 1) + 1
-constexpr uint32_t kBW = 96;            // score-ring slots (the block's 64 columns and 31 before)
-constexpr uint32_t kBD = 8;
-constexpr uint32_t kBRowWords = 128;
-static_assert(kBW >= (uint32_t)(kT - 1 + kBC) && kBW + kBD <= kBRowWords && kBRowWords % 32 == 0 &&
-                  kBW % 32 == 0, "score ring");
-// dynamic shared memory, bytes
-constexpr uint32_t kBOffM = 0;
-constexpr uint32_t kBOffOut = (kM * kM * 4 + 15) & ~15u;             // uint2 [kBWarps][kBRing]
-constexpr uint32_t kBOffStage = kBOffOut + kBWarps * kBRing * 8;     // uint2 [kBWarps][kBC]
-constexpr uint32_t kBOffRed = kBOffStage + kBWarps * kBC * 8;        // 3 words per warp
-constexpr uint32_t kBOffRing = kBOffRed + 128;                       // [kBWarps][A + 1][row]
-__host__ __device__ constexpr uint32_t long_smem_bytes(uint32_t alphabet) {
-    return kBOffRing + kBWarps * (alphabet + 1) * kBRowWords * 4;
-}
-
-// One programme over rows x cols (codes qf(i), df(j)) by the whole block; MODE as in
-// run_dp (0: recurrence (1) and its first maximal cell; 1: anchored at (0, 0), the first
-// cell whose aligned-pair value is S). Every thread returns the block's result.
-template <int MODE, class QF, class DF>
-__device__ void block_dp(const AlignArgs& a, uint8_t* smem, uint2* row7, uint32_t rows,
-                         uint32_t cols, QF qf, DF df, int32_t S, int32_t& best_out,
-                         uint32_t& bi_out, uint32_t& bj_out) {
-    const int32_t border = MODE == 0 ? 0 : kNeg;
-    const int32_t* const M = reinterpret_cast<const int32_t*>(smem + kBOffM);
-    const uint32_t A = a.alphabet;
-    const int w = threadIdx.x >> 5, t = threadIdx.x & 31;
-    const uint32_t smem_s = (uint32_t)__cvta_generic_to_shared(smem);
-    const uint32_t ring_w = smem_s + kBOffRing + (uint32_t)w * (A + 1) * kBRowWords * 4;
-    const uint32_t ring_hi = ring_w + (A + 1) * kBRowWords * 4;
-    auto in_ring = [&](uint32_t at) { return at >= ring_w && at + 4 <= ring_hi; };
-    const uint32_t stage_w = smem_s + kBOffStage + (uint32_t)w * kBC * 8;
-    uint2* const stage_p = reinterpret_cast<uint2*>(smem + kBOffStage) + w * kBC;
-    uint2* const out_ring = reinterpret_cast<uint2*>(smem + kBOffOut);
-    const uint2 kBorder = make_uint2((uint32_t)border, (uint32_t)border);
-
-    const uint32_t nband = (rows + kBBand - 1) / kBBand;
-    const uint32_t ns = (cols + kT - 1 + kBC - 1) / kBC;
-    const uint32_t nbp = ns > (uint32_t)kBMinNBP ? ns : (uint32_t)kBMinNBP;
-    const uint32_t rounds = (nband + kBWarps - 1) / kBWarps;
-    const uint32_t K = kBLag * (kBWarps - 1) + nbp * rounds;
-
-    int32_t best = MODE == 0 ? 0 : S;
-    uint32_t bi = 0xffffffffu, bj = 0xffffffffu;
-    uint32_t cur[kBR];
-    int32_t Hl[kBR], Fr[kBR];
-    int32_t hb_out = border, eb_out = border, hdiag0 = border;
-    uint32_t band = 0;
-    for (uint32_t k = 0; k < K; ++k) {
-        const int64_t g = (int64_t)k - kBLag * w;
-        bool active = false;
-        uint32_t round = 0, b = 0;
-        if (g >= 0) {
-            round = (uint32_t)g / nbp;
-            b = (uint32_t)g % nbp;
-            band = (uint32_t)w + kBWarps * round;
-            active = band < nband && b < ns;
-        }
-        if (active) {
-            const uint32_t c0 = b * kBC;
-            const uint32_t ring_base = round * nbp * kBC;
-            if (b == 0) {
-#pragma unroll
-                for (int l = 0; l < kBR; ++l) {
-                    const uint32_t row = band * kBBand + t * kBR + l;
-                    uint32_t c = row < rows ? qf(row) : A;
-                    if (c > A) c = A;
-                    cur[l] = ring_w + c * kBRowWords * 4;
-                    Hl[l] = border;
-                    Fr[l] = border;
-                }
-                hb_out = eb_out = hdiag0 = border;
-                for (uint32_t i = t; i < A * (kT - 1); i += 32) {  // columns < 0 score 0
-                    const uint32_t at = ring_w + ((i / (kT - 1)) * kBRowWords + kBW - (kT - 1) + i % (kT - 1)) * 4;
-                    if (sw_ok(in_ring(at), a.dbg, 26)) sts_u32(at, 0u);
-                }
-            }
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const uint32_t j = c0 + (uint32_t)t + 32u * h;
-                uint32_t d = j < cols ? df(j) : kPadCode;
-                if (d > kPadCode) d = kPadCode;
-                const uint32_t sl = j % kBW;
-                for (uint32_t c = 0; c < A; ++c) {
-                    const uint32_t v = (uint32_t)M[c * kM + d];
-                    const uint32_t at = ring_w + (c * kBRowWords + sl) * 4;
-                    if (sw_ok(in_ring(at), a.dbg, 26)) sts_u32(at, v);
-                    if (sl < kBD && sw_ok(in_ring(at + kBW * 4), a.dbg, 26)) sts_u32(at + kBW * 4, v);
-                }
-                uint2 top = kBorder;
-                if (j < cols) {
-                    if (w == 0) {
-                        if (band > 0 && sw_ok(j + kT - 1 < a.bstride, a.dbg, 22)) top = row7[j + kT - 1];
-                    } else {
-                        top = out_ring[(w - 1) * kBRing + (ring_base + j + kT - 1) % kBRing];
-                    }
-                }
-                stage_p[t + 32 * h] = top;
-            }
-            __syncwarp();
-            const bool put = t == kT - 1 && band + 1 < nband;
-            uint2* const out = w + 1 < kBWarps ? out_ring + w * kBRing + (ring_base + c0) % kBRing
-                                               : row7 + c0;
-            uint32_t sl = (c0 + kBW - (uint32_t)t) % kBW;
-#pragma unroll 1
-            for (uint32_t sb = 0; sb < (uint32_t)kBC; sb += 8) {
-                uint32_t addr[kBR];
-#pragma unroll
-                for (int l = 0; l < kBR; ++l) addr[l] = cur[l] + sl * 4;
-                const uint32_t st_sb = stage_w + sb * 8;
-                uint2* const out_sb = out + sb;
-#pragma unroll
-                for (int k8 = 0; k8 < 8; ++k8) {
-                    const int32_t h_in = (int32_t)shfl_up_or_lds<kT>((uint32_t)hb_out, st_sb + k8 * 8);
-                    const int32_t e_in = (int32_t)shfl_up_or_lds<kT>((uint32_t)eb_out, st_sb + k8 * 8 + 4);
-                    const int64_t j = (int64_t)c0 + sb + k8 - t;
-                    int32_t diag = hdiag0, E = e_in;
-#pragma unroll
-                    for (int l = 0; l < kBR; ++l) {
-                        const uint32_t i = band * kBBand + (uint32_t)t * kBR + l;
-                        const bool valid = i < rows && j >= 0 && j < (int64_t)cols;
-                        int32_t sc = 0;
-                        if (sw_ok(in_ring(addr[l] + k8 * 4), a.dbg, 26)) sc = (int32_t)lds_u32(addr[l] + k8 * 4);
-                        int32_t H, En, Fn;
-                        if (MODE == 0) {
-                            H = imax(imax(diag + sc, 0), imax(E, Fr[l]));
-                            if (valid && (H > best || (H == best && (i < bi || (i == bi && (uint32_t)j < bj))))) {
-                                best = H;
-                                bi = i;
-                                bj = (uint32_t)j;
-                            }
-                            const int32_t hb = H - a.beta;
-                            En = imax(E - a.alpha, hb);
-                            Fn = imax(Fr[l] - a.alpha, hb);
-                        } else {
-                            const int32_t Mv = (i == 0 && j == 0) ? sc : imax(diag + sc, kNeg);
-                            H = imax(Mv, imax(E, Fr[l]));
-                            if (valid && Mv == S && (i < bi || (i == bi && (uint32_t)j < bj))) {
-                                bi = i;
-                                bj = (uint32_t)j;
-                            }
-                            const int32_t hb = H - a.beta;
-                            En = imax(imax(E - a.alpha, hb), kNeg);
-                            Fn = imax(imax(Fr[l] - a.alpha, hb), kNeg);
-                            if (!valid) {
-                                H = kNeg;
-                                En = kNeg;
-                                Fn = kNeg;
-                            }
-                        }
-                        diag = Hl[l];
-                        Hl[l] = H;
-                        E = En;
-                        Fr[l] = Fn;
-                    }
-                    hb_out = Hl[kBR - 1];
-                    eb_out = E;
-                    hdiag0 = h_in;
-                    if (put && sw_ok(w + 1 < kBWarps || c0 + sb + k8 < a.bstride, a.dbg, 23))
-                        out_sb[k8] = make_uint2((uint32_t)hb_out, (uint32_t)eb_out);
-                }
-                sl = sl + 8 < kBW ? sl + 8 : sl + 8 - kBW;
-            }
-        }
-        __syncthreads();
-    }
-    // the block's first qualifying cell in order of i then j
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const int32_t ob = (int32_t)__shfl_xor_sync(0xffffffffu, (uint32_t)best, o);
-        const uint32_t oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        const uint32_t oj = __shfl_xor_sync(0xffffffffu, bj, o);
-        if (ob > best || (ob == best && (oi < bi || (oi == bi && oj < bj)))) {
-            best = ob;
-            bi = oi;
-            bj = oj;
-        }
-    }
-    uint32_t* const red = reinterpret_cast<uint32_t*>(smem + kBOffRed);
-    if (t == 0) {
-        red[3 * w] = (uint32_t)best;
-        red[3 * w + 1] = bi;
-        red[3 * w + 2] = bj;
-    }
-    __syncthreads();
-    best = (int32_t)red[0];
-    bi = red[1];
-    bj = red[2];
-    for (int v = 1; v < kBWarps; ++v) {
-        const int32_t ob = (int32_t)red[3 * v];
-        const uint32_t oi = red[3 * v + 1], oj = red[3 * v + 2];
-        if (ob > best || (ob == best && (oi < bi || (oi == bi && oj < bj)))) {
-            best = ob;
-            bi = oi;
-            bj = oj;
-        }
-    }
-    __syncthreads();  // the reduction words and the rings are free again
-    best_out = best;
-    bi_out = bi;
-    bj_out = bj;
-}
-
 // Phase 0 (score, end and start cells) of the hits in a.long_list, one block each.
-__global__ void __launch_bounds__(kBThreads) align_long_kernel(const AlignArgs a) {
+__global__ void __launch_bounds__(bw::kThreads) align_long_kernel(const AlignArgs a) {
     extern __shared__ __align__(16) uint8_t smem[];
-    int32_t* const M = reinterpret_cast<int32_t*>(smem + kBOffM);
-    for (uint32_t i = threadIdx.x; i < kM * kM; i += kBThreads) {
-        const uint32_t r = i / kM, c = i % kM;
-        M[i] = (r < a.alphabet && c < a.alphabet) ? (int32_t)a.matrix[r * a.alphabet + c] : 0;
-    }
-    {
-        const int w = threadIdx.x >> 5, t = threadIdx.x & 31;
-        const uint32_t ring_w = (uint32_t)__cvta_generic_to_shared(smem) + kBOffRing +
-                                (uint32_t)w * (a.alphabet + 1) * kBRowWords * 4;
-        for (uint32_t i = t; i < kBRowWords; i += 32)  // row A: query rows past the query
-            sts_u32(ring_w + (a.alphabet * kBRowWords + i) * 4, 0u);
-    }
-    __syncthreads();
+    bw::setup(smem, a.matrix, a.alphabet);
     uint2* const row7 = a.boundary + a.long_row0 + (uint64_t)blockIdx.x * a.bstride;
     for (uint32_t x = blockIdx.x; x < a.n_long; x += gridDim.x) {
         AlignHit& hit = a.hits[a.long_list[x]];
@@ -503,16 +284,18 @@ __global__ void __launch_bounds__(kBThreads) align_long_kernel(const AlignArgs a
         };
         int32_t best = 0;
         uint32_t bi = 0xffffffffu, bj = 0xffffffffu;
-        block_dp<0>(a, smem, row7, qlen, n, [q](uint32_t i) -> uint32_t { return q[i]; }, dcode, 0,
-                    best, bi, bj);
+        bw::block_programme<bw::kFirstMax>(smem, a.alphabet, a.alpha, a.beta, row7, a.bstride, dbg,
+                                           qlen, n, [q](uint32_t i) -> uint32_t { return q[i]; },
+                                           dcode, 0, best, bi, bj);
         uint32_t is = 0, js = 0;
         if (best > 0) {
             const uint32_t ie = bi, je = bj;
             int32_t unused = 0;
             uint32_t ui = 0xffffffffu, uj = 0xffffffffu;
-            block_dp<1>(a, smem, row7, ie + 1, je + 1, [q, ie](uint32_t u) -> uint32_t { return q[ie - u]; },
-                        [dcode, je](uint32_t v) -> uint32_t { return dcode(je - v); }, best, unused, ui,
-                        uj);
+            bw::block_programme<bw::kAnchored>(
+                smem, a.alphabet, a.alpha, a.beta, row7, a.bstride, dbg, ie + 1, je + 1,
+                [q, ie](uint32_t u) -> uint32_t { return q[ie - u]; },
+                [dcode, je](uint32_t v) -> uint32_t { return dcode(je - v); }, best, unused, ui, uj);
             is = ui <= ie ? ie - ui : 0;
             js = uj <= je ? je - uj : 0;
         }
@@ -731,13 +514,13 @@ sw_status align_hits(sw_db* db, const uint8_t* d_queries, int32_t alpha, int32_t
     a.n_long = n_long;
     a.long_row0 = (uint64_t)grid * kWarps * bstride;
     if (n_long) {
-        const uint32_t bytes = long_smem_bytes(db->alphabet);
+        const uint32_t bytes = bw::smem_bytes(db->alphabet);
         if ((e = cudaEventRecord(db->a_ev0, db->stream)) != cudaSuccess ||
             (e = cudaStreamWaitEvent(db->a_stream, db->a_ev0, 0)) != cudaSuccess ||
             (e = cudaFuncSetAttribute(align_long_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)bytes)) != cudaSuccess)
             return cuda_fail(e, "sw_align: long hits");
-        align_long_kernel<<<grid_long, kBThreads, bytes, db->a_stream>>>(a);
+        align_long_kernel<<<grid_long, bw::kThreads, bytes, db->a_stream>>>(a);
         if ((e = cudaGetLastError()) != cudaSuccess ||
             (e = cudaEventRecord(db->a_ev1, db->a_stream)) != cudaSuccess)
             return cuda_fail(e, "sw_align: long hits");

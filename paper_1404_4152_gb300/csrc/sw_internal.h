@@ -11,7 +11,8 @@ namespace swgb {
 // machine): sw_ok(cond, err, site) records the site of the first failed check in the
 // handle's error word and returns false so the caller skips the access. In the normal
 // build it is true and compiles away. Sites: 1-9 search kernels (query profile, ring,
-// stage, matrix table, boundary read / write, database stream), 11-13 rescoring, 21-26
+// stage, matrix table, boundary read / write, database stream), 11-13 the block
+// wavefront (rescoring, long alignment hits: scratch row, database codes, ring), 21-26
 // alignment.
 #ifdef SW_DEBUG_BOUNDS
 constexpr bool kDebugBounds = true;

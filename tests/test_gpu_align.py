@@ -107,7 +107,7 @@ def test_batch_of_queries_matches_single_calls():
 
 @pytest.mark.parametrize("ab", [(1, 11), (5, 2), (0, 5)])
 def test_long_hits_in_the_block_kernel(ab):
-    """Hits of at least 2^21 cells take the score and start-cell programmes in the
+    """Hits of at least 2^20 cells take the score and start-cell programmes in the
     8-warp block kernel (bands of 256 rows, two rounds of warps for a 2,600-row query),
     beside short hits in the one-warp kernel; every alignment must match the oracle's
     letter for letter."""
@@ -122,7 +122,7 @@ def test_long_hits_in_the_block_kernel(ab):
         q[::-1].copy(),                                                  # no long match
         synth.mutate(q[:1000], 33, 3, 2, 300),                           # 2.6 M cells
         flank(820),                                                      # 2.1 M: random
-        flank(300),                                                      # short hits too
+        flank(300),                                                      # 0.8 M: one warp
         synth.mutate(q[1200:1500], 33, 4, 3, 400),
     ]
     res = np.concatenate(seqs)
