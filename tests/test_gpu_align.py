@@ -132,3 +132,25 @@ def test_long_hits_in_the_block_kernel(ab):
         got = _check(db, res, off, q, synth.BLOSUM62, alpha, beta,
                      np.arange(len(seqs), dtype=np.uint64))
     assert got[0]["score"] > 0 and len(got[0]["ops"]) > 2000
+
+
+def test_batch_mixing_long_and_short_hits():
+    """One sw_align_batch call whose hits of two queries fall on both kernels (the block
+    kernel on the second stream and the one-warp kernel); every alignment must match the
+    oracle's letter for letter."""
+    rng = np.random.default_rng(51)
+    qa = synth.make_queries([2600], 52)[0]
+    qb = synth.make_queries([1800], 53)[0]
+    flank = lambda n: synth.make_queries([n], int(rng.integers(1, 1 << 30)))[0]
+    seqs = [synth.mutate(qa, 54, 1, 0, 600), flank(2000), synth.mutate(qb[100:1700], 54, 2, 1, 400),
+            np.concatenate([flank(500), qa[:600], flank(500)]), flank(90), flank(400),
+            synth.mutate(qb, 54, 3, 2, 900)]
+    res = np.concatenate(seqs)
+    off = np.zeros(len(seqs) + 1, np.uint64)
+    off[1:] = np.cumsum([s.size for s in seqs])
+    hits = [(qi, d) for d in range(len(seqs)) for qi in (0, 1)]
+    with sw.sw_db_load(res, off) as db:
+        got = sw.sw_align_batch(db, [qa, qb], synth.BLOSUM62, 1, 11, hits)
+    for (qi, d), g in zip(hits, got):
+        e = oracle.align((qa, qb)[qi], seqs[d], synth.BLOSUM62, 1, 11)
+        assert all(g[k] == e[k] for k in e), (qi, d, g["score"], e["score"])
