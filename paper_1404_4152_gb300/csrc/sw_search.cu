@@ -555,9 +555,21 @@ sw_status enqueue_batch(sw_db* db, uint32_t nq, const uint8_t* d_queries,
     return SW_OK;
 }
 
-namespace {
+// Rows per thread of the query-pair kernel for pairs whose longer queries have these
+// lengths (the server's waves).
+int choose_pair_R(const sw_db* db, const std::vector<uint32_t>& lengths) {
+    return choose_R(db, KernelChoice::kQueryPair, lengths, 3.5);
+}
 
-}  // namespace
+// Whether two queries (la >= lb rows) cost less as one pair in the query-pair kernel,
+// which runs la rows for both, than one after the other in the single-query kernel.
+bool pair_pays(const sw_db* db, uint32_t la, uint32_t lb) {
+    const int R = choose_R(db, KernelChoice::kQueryPair, {la}, 3.5);
+    const double pair = 2.0 * rows_cost(db, KernelChoice::kQueryPair, la, R, 3.5);
+    const KernelChoice a = single_choice(db, la, false), b = single_choice(db, lb, false);
+    const double alone = rows_cost(db, a.mode, la, a.R, 3.9) + rows_cost(db, b.mode, lb, b.R, 3.9);
+    return pair <= alone;
+}
 
 sw_status swgb::check_common(const sw_db* db, uint32_t qlen, int32_t alpha, int32_t beta,
                        uint32_t top_k, const char* fn) {

@@ -182,8 +182,10 @@ sw_status launch_items(sw_server* s, KernelChoice kc, const std::vector<QueryPai
 }
 
 // One wave: every active request advances by one slice. Requests at the same
-// slice are paired (two queries per 16-bit lane pair); one left over at a
-// slice runs alone in the mode that packs two database sequences instead.
+// slice are paired (two queries per 16-bit lane pair) when their lengths are close
+// enough for the pair to cost less than the two alone (the pair runs the longer
+// one's rows for both); the others run alone in the mode that packs two database
+// sequences instead.
 sw_status run_wave(sw_server* s, std::vector<std::shared_ptr<Request>>& act) {
     sw_db* db = s->db;
     cudaError_t e;
@@ -225,7 +227,8 @@ sw_status run_wave(sw_server* s, std::vector<std::shared_ptr<Request>>& act) {
             sc0.push_back(c0);
             sn.push_back(n);
             i += 1;
-        } else if (i + 1 < order.size() && order[i + 1]->next_slice == ra.next_slice) {
+        } else if (i + 1 < order.size() && order[i + 1]->next_slice == ra.next_slice &&
+                   pair_pays(db, (uint32_t)ra.query.size(), (uint32_t)order[i + 1]->query.size())) {
             const Request& rb = *order[i + 1];
             QueryPair p = one(ra);
             p.off_b = (uint64_t)rb.slot * s->max_qlen;
@@ -245,7 +248,11 @@ sw_status run_wave(sw_server* s, std::vector<std::shared_ptr<Request>>& act) {
         }
     }
     sw_status st;
-    if ((st = launch_items(s, KernelChoice{KernelChoice::kQueryPair, 16}, pairs, pc0, pn, 0)))
+    // paired queries: the rows per thread with the least padded cost for their lengths
+    std::vector<uint32_t> plen;
+    for (const QueryPair& p : pairs) plen.push_back(std::max(p.len_a, p.len_b));
+    const int pair_R = pairs.empty() ? 16 : choose_pair_R(db, plen);
+    if ((st = launch_items(s, KernelChoice{KernelChoice::kQueryPair, pair_R}, pairs, pc0, pn, 0)))
         return st;
     // lone queries: the ring with 24 rows per thread, whose short last pass fits any length
     const KernelChoice ks = i32 ? KernelChoice{KernelChoice::kInt32, 16}
