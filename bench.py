@@ -85,9 +85,10 @@ def parse_args():
                         "one GPU's capacity); empty skips serving")
     p.add_argument("--serve-arrivals", type=int, default=16)
     p.add_argument("--long-steps", type=int, default=2,
-                   help="timed searches of the long-sequence workloads (config 4 and 4b; 0 skips)")
+                   help="timed searches of the long-sequence workloads (scores x1 and x3; 0 skips)")
     p.add_argument("--align-top", type=int, default=10,
-                   help="alignments (traceback) of this many top hits per config-1 query (0 skips)")
+                   help="alignments (traceback) of this many top hits per query of the 20-query stream "
+                        "(0 skips)")
     p.add_argument("--no-tune", action="store_true")
     return p.parse_args()
 
@@ -177,12 +178,12 @@ def cpu_oracle_sample(w, seconds: float, threads: int):
 
 
 def build_workload(args, rank):
-    return synth.config1(seed=1405 + 1000 * rank, n_seqs=args.n_seqs, n_queries=args.n_queries)
+    return synth.query_stream(seed=1405 + 1000 * rank, n_seqs=args.n_seqs, n_queries=args.n_queries)
 
 
 def workload_config(w, args, world):
     return {
-        "workload": (f"config1: {len(w.queries)} queries of {min(q.size for q in w.queries)}.."
+        "workload": (f"query_stream: {len(w.queries)} queries of {min(q.size for q in w.queries)}.."
                      f"{max(q.size for q in w.queries)} aa, one at a time, vs {w.n_seqs:,} "
                      f"sequences ({w.db_residues / 1e6:.0f} M aa) per GPU; BLOSUM62, beta={w.beta}, "
                      f"alpha={w.alpha}; every score + top-{w.top_k}"),
@@ -198,7 +199,7 @@ def workload_config(w, args, world):
 def run_batched(args, sw, torch, dev, rank):
     """256 queries (lengths uniform in [50, 2000]) vs 1,000,000 sequences in one
     graph-captured persistent launch per step; GCUPS and the kernel-phase time."""
-    w = synth.config2(seed=1406 + 1000 * rank, n_seqs=args.batch_seqs, n_queries=args.batch_queries)
+    w = synth.query_batch(seed=1406 + 1000 * rank, n_seqs=args.batch_seqs, n_queries=args.batch_queries)
     db = sw.sw_db_load(w.residues, w.offsets, alphabet=20, flags=sw.SW_DB_FLAG_PROFILE)
     if not args.no_tune:
         sw.sw_db_autotune(db, w.matrix, w.alpha, w.beta)
@@ -229,7 +230,7 @@ def run_batched(args, sw, torch, dev, rank):
     prof = sw.sw_db_get_profile(db)
     cells = sum(qlens) * w.db_residues * args.batch_steps
     db.free()
-    return {"workload": f"config2: {nq} queries, lengths uniform [50, 2000] (sum {sum(qlens)}), "
+    return {"workload": f"query_batch: {nq} queries, lengths uniform [50, 2000] (sum {sum(qlens)}), "
                         f"vs {n:,} sequences ({w.db_residues / 1e6:.0f} M aa), one graph-captured "
                         f"persistent launch per step",
             "value": cells / (ms / 1e3) / 1e9, "unit": "GCUPS", "steps": args.batch_steps,
@@ -239,11 +240,11 @@ def run_batched(args, sw, torch, dev, rank):
 def run_long(args, sw, torch, dev, rank):
     """Long sequences: a 5,478-residue query vs 100,000 sequences (mean 2,000, up to 35,000;
     17 % above 3,000 residues go to the warp-per-pair kernel), with 1,000 planted
-    near-duplicates; 4b scales matrix and penalties by 3 so the planted pairs pass the
+    near-duplicates; the second run scales matrix and penalties by 3 so the planted pairs pass the
     16-bit range and are rescored in int32. GCUPS and the per-phase device time."""
     out = []
     for scale in (1, 3):
-        w = synth.config4(seed=1408 + 1000 * rank, scale=scale)
+        w = synth.long_sequences(seed=1408 + 1000 * rank, scale=scale)
         db = sw.sw_db_load(w.residues, w.offsets, alphabet=20, long_threshold=3000,
                            flags=sw.SW_DB_FLAG_PROFILE)
         q = w.queries[0]
@@ -288,8 +289,8 @@ def run_long(args, sw, torch, dev, rank):
 
 
 def run_traceback(args, sw, w, db, top_index, qlens):
-    """Alignments of the top hits of every config-1 query through sw_align (host buffers,
-    wall clock; the second of two rounds is timed), with the dynamic-programming cells of
+    """Alignments of the top hits of every query of the 20-query stream through sw_align
+    (host buffers, wall clock; the second of two rounds is timed), with the dynamic-programming cells of
     its three passes, and the oracle's traceback of a few of them on the host for scale."""
     import oracle
 
@@ -328,7 +329,7 @@ def run_traceback(args, sw, w, db, top_index, qlens):
     for i in range(len(qlens)):
         sw.sw_align(db, w.queries[i], w.matrix, w.alpha, w.beta, idx[i][:1])
     gpu_top = time.perf_counter() - t0
-    return {"workload": f"top {k} hits of each of the {len(qlens)} config-1 queries: one optimal "
+    return {"workload": f"top {k} hits of each of the {len(qlens)} stream queries: one optimal "
                         f"alignment each (score, end and start cells, op string), all in one "
                         f"sw_align_batch call",
             "alignments": n_al, "ms": secs * 1e3, "alignments_per_s": n_al / secs,
@@ -354,7 +355,7 @@ def run_served(args, sw, rank):
     del res
     out = []
     for ri, rate in enumerate(rates):
-        lens = synth.config3_query_lengths(args.serve_arrivals, 1407 + ri)
+        lens = synth.served_query_lengths(args.serve_arrivals, 1407 + ri)
         qs = synth.make_queries(lens, 1407 + ri)
         arrive = synth.arrival_times(len(qs), rate, 1407 + ri)
         srv = sw.sw_server_create(db, max_active=32, slices=8)
@@ -394,7 +395,7 @@ def run_served(args, sw, rank):
                     "busy_gcups": cells / (st["busy_ms"] / 1e3) / 1e9 if st["busy_ms"] else None,
                     "waves": st["waves"]})
     db.free()
-    return {"workload": f"config3: {args.serve_seqs:,} resident sequences ({n_res / 1e9:.2f} G aa); "
+    return {"workload": f"served_stream: {args.serve_seqs:,} resident sequences ({n_res / 1e9:.2f} G aa); "
                         f"Poisson arrivals, query lengths log-normal median 300 [20, 5000]; "
                         f"32 query slots, 8 slices",
             "rates": out}

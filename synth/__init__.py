@@ -249,41 +249,41 @@ def make_queries(lengths, seed: int) -> list:
     return [res[int(off[i]):int(off[i + 1])].copy() for i in range(len(lengths))]
 
 
-def config1_query_lengths() -> list:
+def stream_query_lengths() -> list:
     """20 lengths geometrically spaced from 144 to 5,478 (the paper's query range)."""
     return [int(math.floor(144.0 * (5478.0 / 144.0) ** (k / 19.0) + 0.5)) for k in range(20)]
 
 
-def config0(seed: int = 1404) -> Workload:
+def small_search(seed: int = 1404) -> Workload:
     """One 144-residue query against 10,000 sequences; BLOSUM62, beta=11, alpha=1, top 10."""
     res, off = make_db(10_000, seed)
-    return Workload("config0", res, off, make_queries([144], seed), BLOSUM62.copy(), 1, 11, 10)
+    return Workload("small_search", res, off, make_queries([144], seed), BLOSUM62.copy(), 1, 11, 10)
 
 
-def config1(seed: int = 1405, n_seqs: int = 2_000_000, n_queries: int = 20) -> Workload:
+def query_stream(seed: int = 1405, n_seqs: int = 2_000_000, n_queries: int = 20) -> Workload:
     """20 queries of 144..5478 residues (one at a time) against 2,000,000 sequences."""
     res, off = make_db(n_seqs, seed)
-    qs = make_queries(config1_query_lengths()[:n_queries], seed)
-    return Workload("config1", res, off, qs, BLOSUM62.copy(), 1, 11, 10)
+    qs = make_queries(stream_query_lengths()[:n_queries], seed)
+    return Workload("query_stream", res, off, qs, BLOSUM62.copy(), 1, 11, 10)
 
 
-def config2(seed: int = 1406, n_seqs: int = 1_000_000, n_queries: int = 256) -> Workload:
+def query_batch(seed: int = 1406, n_seqs: int = 1_000_000, n_queries: int = 256) -> Workload:
     """256 queries with lengths uniform in [50, 2000] against 1,000,000 sequences."""
     res, off = make_db(n_seqs, seed)
     lens = uniform_u32(n_queries, 50, 2000, seed, _S_Q_LEN)
-    return Workload("config2", res, off, make_queries(lens, seed), BLOSUM62.copy(), 1, 11, 10)
+    return Workload("query_batch", res, off, make_queries(lens, seed), BLOSUM62.copy(), 1, 11, 10)
 
 
-def config3_query_lengths(n: int, seed: int) -> np.ndarray:
+def served_query_lengths(n: int, seed: int) -> np.ndarray:
     """Serving queries: log-normal, median 300, sigma 0.642, clipped to [20, 5000]."""
     qt = _qtable(math.log(300.0), 0.642, 20, 5000)
     return gen_lengths(n, qt, seed, _S_Q_LEN)
 
 
-def config3(seed: int = 1407, n_seqs: int = 20_000_000, n_queries: int = 200) -> Workload:
+def served_stream(seed: int = 1407, n_seqs: int = 20_000_000, n_queries: int = 200) -> Workload:
     res, off = make_db(n_seqs, seed)
-    qs = make_queries(config3_query_lengths(n_queries, seed), seed)
-    return Workload("config3", res, off, qs, BLOSUM62.copy(), 1, 11, 10)
+    qs = make_queries(served_query_lengths(n_queries, seed), seed)
+    return Workload("served_stream", res, off, qs, BLOSUM62.copy(), 1, 11, 10)
 
 
 def arrival_times(n: int, rate_per_s: float, seed: int) -> np.ndarray:
@@ -293,7 +293,7 @@ def arrival_times(n: int, rate_per_s: float, seed: int) -> np.ndarray:
     return np.cumsum(-np.log(u) / rate_per_s)
 
 
-def config4(seed: int = 1408, n_seqs: int = 100_000, n_planted: int = 1000,
+def long_sequences(seed: int = 1408, n_seqs: int = 100_000, n_planted: int = 1000,
             scale: int = 1) -> Workload:
     """A 5,478-residue query against 100,000 long-ish sequences (mean 2000, up to 35,000)
     with near-duplicates of the query (5% substitutions) planted at random positions.
@@ -312,6 +312,7 @@ def config4(seed: int = 1408, n_seqs: int = 100_000, n_planted: int = 1000,
     for k, p in enumerate(pos):
         res[int(off[p]):int(off[p + 1])] = mutate(q, seed, _S_PLANT_MUT, k, 500)
     m = (BLOSUM62.astype(np.int32) * scale).astype(np.int8)
-    w = Workload(f"config4{'b' if scale > 1 else ''}", res, off, [q], m, 1 * scale, 11 * scale, 10)
+    w = Workload(f"long_sequences{'_x3' if scale == 3 else f'_x{scale}' if scale > 1 else ''}", res, off,
+                 [q], m, 1 * scale, 11 * scale, 10)
     w.notes["planted"] = pos
     return w

@@ -32,7 +32,7 @@ def _check(db, res, off, q, M, alpha, beta, idx):
 
 
 def test_top_hits_and_random_sequences():
-    w = synth.config0()
+    w = synth.small_search()
     q = w.queries[0]
     with sw.sw_db_load(w.residues, w.offsets) as db:
         _, ts, ti, _ = sw.sw_search(db, q, w.matrix, w.alpha, w.beta, 20, want_scores=False)
@@ -89,7 +89,7 @@ def test_scores_beyond_16_bits_and_edge_cases():
 
 
 def test_batch_of_queries_matches_single_calls():
-    w = synth.config0()
+    w = synth.small_search()
     qs = synth.make_queries([144, 700, 37, 1500], 41)
     with sw.sw_db_load(w.residues, w.offsets) as db:
         hits, singles = [], []

@@ -29,7 +29,7 @@ def _check_sampled(w, q, scores, ts, ti, sample, extra=()):
 
 
 def test_two_million_sequences_sampled():
-    w = synth.config1()
+    w = synth.query_stream()
     with sw.sw_db_load(w.residues, w.offsets) as db:
         for q in (w.queries[0], w.queries[10], w.queries[19]):
             scores, ts, ti, st = sw.sw_search(db, q, w.matrix, w.alpha, w.beta, w.top_k)
@@ -41,7 +41,7 @@ def test_long_sequences_and_planted_duplicates(scale):
     """A 5,478-residue query against 100,000 sequences of mean length 2,000 (up to 35,000),
     1,000 of them near-copies of the query. scale 3 multiplies the matrix and penalties by 3,
     which pushes the planted pairs past the 16-bit range and through int32 rescoring."""
-    w = synth.config4(scale=scale)
+    w = synth.long_sequences(scale=scale)
     q = w.queries[0]
     planted = w.notes["planted"]
     with sw.sw_db_load(w.residues, w.offsets, long_threshold=3000) as db:
@@ -56,9 +56,10 @@ def test_long_sequences_and_planted_duplicates(scale):
 
 
 def test_traceback_of_planted_long_pairs_above_16_bits():
-    """Config 4b (matrix and penalties x3): alignments of planted 5,478-residue near-copies
-    whose scores pass the 16-bit range, letter for letter against the oracle."""
-    w = synth.config4(scale=3)
+    """The long-sequence workload with matrix and penalties x3: alignments of planted
+    5,478-residue near-copies whose scores pass the 16-bit range, letter for letter
+    against the oracle."""
+    w = synth.long_sequences(scale=3)
     q = w.queries[0]
     planted = np.asarray(w.notes["planted"][:6], dtype=np.uint64)
     rng = np.random.default_rng(5)

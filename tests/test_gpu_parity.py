@@ -48,8 +48,8 @@ def _check(db, res, off, q, M, alpha, beta, k, *, expect_recompute=None):
     return scores, stats
 
 
-def test_config0_full(kflags):
-    w = synth.config0()
+def test_small_search_full(kflags):
+    w = synth.small_search()
     with sw.sw_db_load(w.residues, w.offsets, flags=kflags) as db:
         _check(db, w.residues, w.offsets, w.queries[0], w.matrix, w.alpha, w.beta, w.top_k,
                expect_recompute=False)
@@ -160,7 +160,7 @@ def test_top_k_larger_than_database():
 
 
 def test_repeated_searches_same_handle():
-    w = synth.config0()
+    w = synth.small_search()
     off = w.offsets[:3001].copy()
     res = w.residues[: int(off[-1])]
     qs = synth.make_queries([144, 600, 37, 2100], 12)
@@ -171,7 +171,7 @@ def test_repeated_searches_same_handle():
 
 def test_device_api_with_torch_buffers():
     torch = pytest.importorskip("torch")
-    w = synth.config0()
+    w = synth.small_search()
     off = w.offsets[:2001].copy()
     res = w.residues[: int(off[-1])]
     q = w.queries[0]
@@ -193,7 +193,7 @@ def test_device_api_with_torch_buffers():
 
 
 def test_batch_matches_single():
-    w = synth.config0()
+    w = synth.small_search()
     off = w.offsets[:1500].copy()
     res = w.residues[: int(off[-1])]
     qs = synth.make_queries([80, 144, 500], 21)

@@ -174,7 +174,7 @@ def test_top_k_order_and_ties():
 
 
 def test_search_matches_pairwise():
-    w = synth.config0()
+    w = synth.small_search()
     q = w.queries[0]
     sub = 300
     off = w.offsets[: sub + 1]

@@ -54,7 +54,7 @@ def _worker(rank, world, port, q):
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
-    w = synth.config0()
+    w = synth.small_search()
     n = 1200
     off = w.offsets[: n + 1]
     res = w.residues[: int(off[-1])]
@@ -80,7 +80,7 @@ def test_two_rank_allgather_top_k():
     for p in procs:
         p.join(timeout=60)
         assert p.exitcode == 0
-    w = synth.config0()
+    w = synth.small_search()
     off = w.offsets[:1201]
     full = oracle.scores(w.queries[0], w.residues[: int(off[-1])], off, w.matrix, w.alpha, w.beta)
     es, ei = pins.ranked_top_k(full, 10)

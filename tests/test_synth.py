@@ -38,8 +38,8 @@ def test_database_shape():
 
 
 def test_config_shapes():
-    assert synth.config1_query_lengths()[0] == 144 and synth.config1_query_lengths()[-1] == 5478
-    w = synth.config4(n_seqs=2000, n_planted=20)
+    assert synth.stream_query_lengths()[0] == 144 and synth.stream_query_lengths()[-1] == 5478
+    w = synth.long_sequences(n_seqs=2000, n_planted=20)
     assert w.queries[0].size == 5478
     pos = w.notes["planted"]
     for p in pos:
