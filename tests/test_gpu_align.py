@@ -154,3 +154,29 @@ def test_batch_mixing_long_and_short_hits():
     for (qi, d), g in zip(hits, got):
         e = oracle.align((qa, qb)[qi], seqs[d], synth.BLOSUM62, 1, 11)
         assert all(g[k] == e[k] for k in e), (qi, d, g["score"], e["score"])
+
+
+@pytest.mark.parametrize("A", [3, 32])
+def test_long_hits_other_alphabets(A):
+    """The block kernel's score rings hold A + 1 code rows (the most shared memory at
+    A = 32); long hits over other alphabets, with an asymmetric matrix, must still match
+    the oracle letter for letter."""
+    rng = np.random.default_rng(400 + A)
+    M = rng.integers(-4, 5, size=(A, A)).astype(np.int8)
+    np.fill_diagonal(M, 6)
+    q = rng.integers(0, A, size=1500).astype(np.uint8)
+
+    def mutated(x, rate):
+        y = x.copy()
+        hit = rng.random(y.size) < rate
+        y[hit] = rng.integers(0, A, size=int(hit.sum()))
+        return y
+
+    seqs = [mutated(q, 0.1), np.concatenate([rng.integers(0, A, 400).astype(np.uint8),
+                                              mutated(q[300:1200], 0.05)]),
+            rng.integers(0, A, 1100).astype(np.uint8), rng.integers(0, A, 200).astype(np.uint8)]
+    res = np.concatenate(seqs)
+    off = np.zeros(len(seqs) + 1, np.uint64)
+    off[1:] = np.cumsum([s.size for s in seqs])
+    with sw.sw_db_load(res, off, alphabet=A) as db:
+        _check(db, res, off, q, M, 1, 7, np.arange(len(seqs), dtype=np.uint64))
