@@ -25,7 +25,8 @@ included). GCUPS = sum(|query|) * sum(|db sequence|) / seconds.
 
 --impl reference times the CPU oracle itself as the reference arm.
 Under torchrun each rank searches its own database shard (weak scaling); the
-JSON line reports the slowest rank's time.
+JSON line reports the slowest rank's time, and the batched, served, long-sequence
+and traceback legs (single-GPU measurements) are skipped.
 """
 from __future__ import annotations
 
@@ -443,8 +444,17 @@ def run_ours(args):
 
     from paper_1404_4152_gb300 import build as swbuild
 
-    swbuild.build()
+    # one rank builds (or finds the build current); the others wait for it
+    if rank == 0:
+        swbuild.build()
+    if world > 1:
+        torch.distributed.barrier()
     import paper_1404_4152_gb300 as sw
+
+    if world > 1:
+        # the scaling runs time the headline search (and its e2e) only; the batched,
+        # served, long-sequence and traceback legs are single-GPU measurements
+        args.batch_steps, args.serve_rates, args.long_steps, args.align_top = 0, "", 0, 0
 
     w = build_workload(args, rank)
     db = sw.sw_db_load(w.residues, w.offsets, alphabet=20, device=local, flags=sw.SW_DB_FLAG_PROFILE)
