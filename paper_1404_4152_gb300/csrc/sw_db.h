@@ -151,8 +151,9 @@ sw_status db_alloc(sw_db* db, void** p, size_t bytes, const char* what);
 // Rows per thread of the query-pair kernel for pairs whose longer queries have these
 // lengths: the tuned (or estimated) cost of their padded rows (sw_search.cu).
 int choose_pair_R(const sw_db* db, const std::vector<uint32_t>& lengths);
-// Whether queries of la >= lb rows cost less paired in the query-pair kernel than alone.
-bool pair_pays(const sw_db* db, uint32_t la, uint32_t lb);
+// Whether queries of la >= lb rows cost less paired in the query-pair kernel than each
+// alone in the kernel `alone`.
+bool pair_pays(const sw_db* db, uint32_t la, uint32_t lb, swgb::KernelChoice alone);
 // Allocate the per-handle search scratch (boundary rows, counters, top-k).
 sw_status sw_db_prepare_search(sw_db* db);
 sw_status ensure(sw_db* db, DevBuf& b, size_t bytes, const char* what);

@@ -562,13 +562,13 @@ int choose_pair_R(const sw_db* db, const std::vector<uint32_t>& lengths) {
 }
 
 // Whether two queries (la >= lb rows) cost less as one pair in the query-pair kernel,
-// which runs la rows for both, than one after the other in the single-query kernel.
-bool pair_pays(const sw_db* db, uint32_t la, uint32_t lb) {
+// which runs la rows for both, than one after the other in the kernel `alone`.
+bool pair_pays(const sw_db* db, uint32_t la, uint32_t lb, swgb::KernelChoice alone) {
     const int R = choose_R(db, KernelChoice::kQueryPair, {la}, 3.5);
     const double pair = 2.0 * rows_cost(db, KernelChoice::kQueryPair, la, R, 3.5);
-    const KernelChoice a = single_choice(db, la, false), b = single_choice(db, lb, false);
-    const double alone = rows_cost(db, a.mode, la, a.R, 3.9) + rows_cost(db, b.mode, lb, b.R, 3.9);
-    return pair <= alone;
+    const double apart = rows_cost(db, alone.mode, la, alone.R, 3.9) +
+                         rows_cost(db, alone.mode, lb, alone.R, 3.9);
+    return pair <= apart;
 }
 
 sw_status swgb::check_common(const sw_db* db, uint32_t qlen, int32_t alpha, int32_t beta,

@@ -195,6 +195,11 @@ sw_status run_wave(sw_server* s, std::vector<std::shared_ptr<Request>>& act) {
         return x->query.size() > y->query.size();
     });
     const bool i32 = (int64_t)s->scheme_alpha + s->scheme_beta > 32768;
+    // lone queries: the ring with 24 rows per thread, whose short last pass fits any length
+    const KernelChoice ks = i32 ? KernelChoice{KernelChoice::kInt32, 16}
+                          : (db->flags & SW_DB_FLAG_QUERY_PROFILE)
+                              ? KernelChoice{KernelChoice::kPairDb, 16}
+                              : KernelChoice{KernelChoice::kPairRing, kRingLastR};
     auto one = [&](const Request& r) {
         QueryPair p{};
         p.off_a = p.off_b = (uint64_t)r.slot * s->max_qlen;
@@ -228,7 +233,7 @@ sw_status run_wave(sw_server* s, std::vector<std::shared_ptr<Request>>& act) {
             sn.push_back(n);
             i += 1;
         } else if (i + 1 < order.size() && order[i + 1]->next_slice == ra.next_slice &&
-                   pair_pays(db, (uint32_t)ra.query.size(), (uint32_t)order[i + 1]->query.size())) {
+                   pair_pays(db, (uint32_t)ra.query.size(), (uint32_t)order[i + 1]->query.size(), ks)) {
             const Request& rb = *order[i + 1];
             QueryPair p = one(ra);
             p.off_b = (uint64_t)rb.slot * s->max_qlen;
@@ -254,11 +259,6 @@ sw_status run_wave(sw_server* s, std::vector<std::shared_ptr<Request>>& act) {
     const int pair_R = pairs.empty() ? 16 : choose_pair_R(db, plen);
     if ((st = launch_items(s, KernelChoice{KernelChoice::kQueryPair, pair_R}, pairs, pc0, pn, 0)))
         return st;
-    // lone queries: the ring with 24 rows per thread, whose short last pass fits any length
-    const KernelChoice ks = i32 ? KernelChoice{KernelChoice::kInt32, 16}
-                          : (db->flags & SW_DB_FLAG_QUERY_PROFILE)
-                              ? KernelChoice{KernelChoice::kPairDb, 16}
-                              : KernelChoice{KernelChoice::kPairRing, kRingLastR};
     if ((st = launch_items(s, ks, singles, sc0, sn, 1))) return st;
     if (!i32) {
         RescoreArgs r{};
