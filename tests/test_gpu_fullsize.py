@@ -72,3 +72,17 @@ def test_traceback_of_planted_long_pairs_above_16_bits():
         e = oracle.align(q, d, w.matrix, w.alpha, w.beta)
         assert all(g[k] == e[k] for k in e), (int(i), g["score"], e["score"])
     assert min(g["score"] for g in got[:6]) > 32767
+
+
+def test_batch_of_256_queries_against_a_million_sequences_sampled():
+    """The batched workload as the benchmark runs it (256 queries, lengths uniform in
+    [50, 2000], against 1,000,000 sequences, one graph-captured launch): for a seeded sample
+    of 24 queries, a sample of scores and every top-k hit against the oracle, and each
+    top-k list against the ranked top-k of its returned row."""
+    w = synth.query_batch()
+    with sw.sw_db_load(w.residues, w.offsets) as db:
+        rows, ts, ti, nt, st = sw.sw_search_batch(db, w.queries, w.matrix, w.alpha, w.beta,
+                                                  w.top_k, want_scores=True)
+    rng = np.random.default_rng(11)
+    for qi in sorted(rng.choice(len(w.queries), size=24, replace=False).tolist()):
+        _check_sampled(w, w.queries[qi], rows[qi], ts[qi], ti[qi], sample=60)
