@@ -86,3 +86,21 @@ def test_batch_of_256_queries_against_a_million_sequences_sampled():
     rng = np.random.default_rng(11)
     for qi in sorted(rng.choice(len(w.queries), size=24, replace=False).tolist()):
         _check_sampled(w, w.queries[qi], rows[qi], ts[qi], ti[qi], sample=60)
+
+
+def test_served_stream_at_full_size_matches_plain_search():
+    """The serving workload's resident database (20,000,000 sequences, 7 G residues): eight
+    queries of the served length mix submitted together, so waves pair some of them and run
+    others alone over 8 slices; every top-k list must equal the single-query search's on the
+    same handle, and its hits' scores the oracle's."""
+    res, off = synth.make_db(20_000_000, 1407)
+    qs = synth.make_queries(synth.served_query_lengths(8, 1417), 1417)
+    with sw.sw_db_load(res, off) as db:
+        plain = [sw.sw_search(db, q, synth.BLOSUM62, 1, 11, 10, want_scores=False) for q in qs]
+        with sw.sw_server_create(db, max_active=8, slices=8) as srv:
+            tickets = [srv.submit(q, synth.BLOSUM62, 1, 11, 10) for q in qs]
+            got = [srv.wait(t) for t in tickets]
+    for q, (s, ts, ti, _), g in zip(qs, plain, got):
+        assert np.array_equal(g[0], ts) and np.array_equal(g[1], ti)
+        es = oracle.scores(q, res, off, synth.BLOSUM62, 1, 11, which=ti.astype(np.int64))
+        assert np.array_equal(es, ts)
