@@ -380,7 +380,10 @@ sw_status sw_search_noalloc(const uint8_t* d_query, uint32_t qlen, const int8_t*
  *
  * Scores are computed in int32 whatever the penalties. Device memory: the box
  * between the start and end cells takes one byte per cell (batched within
- * 1 GiB; a larger single box takes its own size).
+ * 1 GiB; a larger single box takes its own size). Hits of at least 2^20 cells
+ * (query length x sequence length) find their end and start cells on a whole
+ * block of warps, on a second stream the handle creates on first use; the call
+ * returns when both streams are done.
  */
 typedef struct {
     int32_t score;
@@ -411,8 +414,8 @@ sw_status sw_align_batch(sw_db* db, uint32_t nq, const uint8_t* queries, const u
  * global-memory indices, skip an access that would leave its buffer and record
  * the site of the first such access in the handle. This call waits for the
  * device, returns that site (0: none) and clears it. In the normal build it
- * always returns 0. Sites: 1-8 search kernels, 11-13 rescoring, 21-25
- * alignment.
+ * always returns 0. Sites: 1-8 search kernels, 11-13 the block-wide kernels
+ * (int32 rescoring, long alignment hits), 21-26 alignment.
  */
 sw_status sw_db_debug_check(sw_db* db, uint32_t* site);
 
