@@ -30,6 +30,8 @@ struct BatchGraph {
     cudaStream_t stream = nullptr;
     std::vector<uint64_t> qoff;
     std::vector<uint32_t> qlen;
+    std::vector<int> group_R;           // the launches: rows per thread and first pair
+    std::vector<uint32_t> group_first;
     uint32_t kernels = 0;
 };
 

@@ -369,11 +369,17 @@ sw_status enqueue_search(sw_db* db, const uint8_t* d_query, uint32_t qlen, const
 
 namespace {
 
+// Pairs grouped by the rows per thread each runs best at; group g is pairs
+// [group_first[g], group_first[g + 1]) with group_R[g] rows per thread.
+constexpr int kMaxGroups = 5;   // one per rows-per-thread choice
+constexpr int kGroupCounter0 = 16;  // the groups' work counters: d_counters[16 ..]
+
 struct BatchPlan {
     std::vector<QueryPair> pairs;
     std::vector<uint64_t> qoff;
     std::vector<uint32_t> qlen;
-    KernelChoice kc{KernelChoice::kQueryPair, 16};
+    std::vector<int> group_R;
+    std::vector<uint32_t> group_first;
     uint64_t cells = 0;
     uint32_t flag_cap = 0;
 };
@@ -408,7 +414,21 @@ BatchPlan plan_batch(const sw_db* db, uint32_t nq, const uint64_t* qoffsets) {
         pl.pairs.push_back(p);
         item_len.push_back(std::max(p.len_a, p.len_b));
     }
-    pl.kc = KernelChoice{KernelChoice::kQueryPair, choose_R(db, 1, item_len, 3.5)};
+    // each pair takes the rows per thread of its least padded cost; pairs of one choice
+    // run in one launch (longest first inside each, as sorted)
+    std::vector<int> best_R(pl.pairs.size());
+    for (size_t i = 0; i < pl.pairs.size(); ++i) best_R[i] = choose_R(db, 1, {item_len[i]}, 3.5);
+    std::vector<QueryPair> grouped;
+    pl.group_first.push_back(0);
+    for (int R : kShortR) {
+        for (size_t i = 0; i < pl.pairs.size(); ++i)
+            if (best_R[i] == R) grouped.push_back(pl.pairs[i]);
+        if (grouped.size() > pl.group_first.back()) {
+            pl.group_R.push_back(R);
+            pl.group_first.push_back((uint32_t)grouped.size());
+        }
+    }
+    pl.pairs.swap(grouped);
     for (uint32_t q = 0; q < nq; ++q) pl.cells += (uint64_t)pl.qlen[q] * db->total_residues;
     pl.flag_cap = (uint32_t)std::min<uint64_t>(std::max<uint64_t>(db->n_seqs, 1u << 20), 1u << 26);
     return pl;
@@ -443,16 +463,22 @@ sw_status launch_batch(sw_db* db, const BatchPlan& pl, const uint8_t* d_queries,
                        cudaStream_t stream) {
     cudaError_t e;
     const uint32_t nq = (uint32_t)pl.qlen.size();
-    if ((e = cudaMemsetAsync(db->d_counters, 0, 64, stream)) != cudaSuccess)
+    static_assert(kGroupCounter0 + kMaxGroups <= kDebugWord, "counter words");
+    if ((e = cudaMemsetAsync(db->d_counters, 0, (kGroupCounter0 + kMaxGroups) * 4, stream)) !=
+        cudaSuccess)
         return cuda_fail(e, "batch: counter reset");
     WavefrontArgs a = base_args(db, d_matrix, alpha, beta, d_scores, db->n_seqs, kTileSeqs);
     a.query = d_queries;
-    a.pairs = (const QueryPair*)db->b_pairs.p;
-    a.n_pairs = (uint32_t)pl.pairs.size();
     a.flag_list = (uint2*)db->b_flags.p;
     a.flag_cap = pl.flag_cap;
-    if ((e = launch_wavefront(pl.kc, a, grid_for(db, pl.kc), stream)) != cudaSuccess)
-        return cuda_fail(e, "batch: wavefront kernel");
+    for (size_t g = 0; g < pl.group_R.size(); ++g) {  // one launch per rows-per-thread group
+        const KernelChoice kc{KernelChoice::kQueryPair, pl.group_R[g]};
+        a.pairs = (const QueryPair*)db->b_pairs.p + pl.group_first[g];
+        a.n_pairs = pl.group_first[g + 1] - pl.group_first[g];
+        a.work_counter = db->d_counters + kGroupCounter0 + g;
+        if ((e = launch_wavefront(kc, a, grid_for(db, kc), stream)) != cudaSuccess)
+            return cuda_fail(e, "batch: wavefront kernel");
+    }
     RescoreArgs r = rescore_args(db, d_matrix, alpha, beta, d_scores, db->n_seqs);
     r.list = (const uint2*)db->b_flags.p;
     r.cap = pl.flag_cap;
@@ -477,7 +503,8 @@ bool same_key(const BatchGraph& g, const BatchPlan& pl, const void* q, const voi
               const void* ti, cudaStream_t st) {
     return g.exec && g.queries == q && g.matrix == m && g.alpha == alpha && g.beta == beta &&
            g.top_k == k && g.scores == s && g.top_s == ts && g.top_i == ti && g.stream == st &&
-           g.qoff == pl.qoff && g.qlen == pl.qlen;
+           g.qoff == pl.qoff && g.qlen == pl.qlen && g.group_R == pl.group_R &&
+           g.group_first == pl.group_first;
 }
 
 }  // namespace
@@ -545,7 +572,9 @@ sw_status enqueue_batch(sw_db* db, uint32_t nq, const uint8_t* d_queries,
         g.stream = stream;
         g.qoff = pl.qoff;
         g.qlen = pl.qlen;
-        g.kernels = 2 + (top_k ? topk_launch_count() : 0);
+        g.group_R = pl.group_R;
+        g.group_first = pl.group_first;
+        g.kernels = (uint32_t)pl.group_R.size() + 1 + (top_k ? topk_launch_count() : 0);
     }
     PhaseTimer pt(db, 3, stream, pl.cells);
     if ((e = cudaGraphLaunch(g.exec, stream)) != cudaSuccess)
