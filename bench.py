@@ -17,7 +17,8 @@ included). GCUPS = sum(|query|) * sum(|db sequence|) / seconds.
              algorithmic ALU lane-operations / its mean launch time, against the
              ALU-pipe peak at the SM clock sampled during the run.
   cpu_baseline  the CPU oracle on a bounded sample of the same workload.
-  batched    256 queries against 1,000,000 sequences in one graph-captured launch.
+  batched    256 queries against 1,000,000 sequences in one graph-captured batch
+             (a persistent launch per rows-per-thread group of query pairs).
   served     the continuous-batching server over 20,000,000 resident sequences,
              Poisson arrivals: p50 / p99 latency and sustained GCUPS per rate.
   long_sequences  a 5,478-residue query against 100,000 long sequences (the
@@ -199,7 +200,8 @@ def workload_config(w, args, world):
 
 def run_batched(args, sw, torch, dev, rank):
     """256 queries (lengths uniform in [50, 2000]) vs 1,000,000 sequences in one
-    graph-captured persistent launch per step; GCUPS and the kernel-phase time."""
+    graph-captured batch per step (a persistent launch per rows-per-thread group of query
+    pairs); GCUPS and the kernel-phase time."""
     w = synth.query_batch(seed=1406 + 1000 * rank, n_seqs=args.batch_seqs, n_queries=args.batch_queries)
     db = sw.sw_db_load(w.residues, w.offsets, alphabet=20, flags=sw.SW_DB_FLAG_PROFILE)
     if not args.no_tune:
@@ -233,7 +235,7 @@ def run_batched(args, sw, torch, dev, rank):
     db.free()
     return {"workload": f"query_batch: {nq} queries, lengths uniform [50, 2000] (sum {sum(qlens)}), "
                         f"vs {n:,} sequences ({w.db_residues / 1e6:.0f} M aa), one graph-captured "
-                        f"persistent launch per step",
+                        f"batch per step (a persistent launch per rows-per-thread group)",
             "value": cells / (ms / 1e3) / 1e9, "unit": "GCUPS", "steps": args.batch_steps,
             "ms_per_step": ms / args.batch_steps, "gpu_launches": int(prof["launches"])}
 
