@@ -150,7 +150,6 @@ struct RescoreArgs {
     uint32_t* dbg;                  // error word of the bounds-checked build (may be NULL)
 };
 cudaError_t launch_rescore(const RescoreArgs& a, int grid, cudaStream_t stream);
-int rescore_block_threads();
 int rescore_blocks_per_sm(uint32_t alphabet);  // resident blocks per SM for this alphabet
 
 // Entries past a unit's length that a boundary row half must hold (per half:

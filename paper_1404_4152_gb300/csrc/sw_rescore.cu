@@ -67,8 +67,6 @@ cudaError_t launch_rescore(const RescoreArgs& a, int grid, cudaStream_t stream) 
     return cudaGetLastError();
 }
 
-int rescore_block_threads() { return bw::kThreads; }
-
 int rescore_blocks_per_sm(uint32_t alphabet) {
     const uint32_t bytes = bw::smem_bytes(alphabet);
     if (cudaFuncSetAttribute(rescore_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
