@@ -260,9 +260,11 @@ sw_status sw_db_autotune(sw_db* db, const int8_t* matrix, int32_t alpha, int32_t
  * queries as they arrive).
  *
  * The database is cut into `slices` parts of about equal work. A scheduler
- * thread runs waves; one wave advances every admitted query by one slice in a
- * single persistent launch (two queries at the same slice share the 16-bit
- * lane halves). A query is admitted at a wave boundary when a slot is free: a
+ * thread runs waves; one wave advances every admitted query by one slice in
+ * persistent launches (two queries at the same slice share the 16-bit lane
+ * halves when their lengths are close enough for the pair to cost less than
+ * the two alone; the others run one query against two sequences). A query is
+ * admitted at a wave boundary when a slot is free: a
  * slot reserves the device memory one query needs (a score row of n_seqs
  * int32 and max_qlen code bytes), and the number of slots is bounded by
  * max_active and by device_budget, so admission is by device memory. Queries
