@@ -5,9 +5,9 @@
 //  - the database is cut into S slices of about equal work (contiguous runs of
 //    length-sorted chunks);
 //  - a scheduler thread runs waves; one wave advances every admitted query by
-//    one slice, in a single persistent launch whose work items are (query
-//    pair, chunk of that pair's slice) -- two queries at the same slice share
-//    the two 16-bit halves of the lanes;
+//    one slice, in persistent launches whose work items are (query or query
+//    pair, chunk of its slice) -- two queries at the same slice share the two
+//    16-bit halves of the lanes when the pair costs less than the two alone;
 //  - a query is admitted at a wave boundary when a slot is free: a slot is the
 //    device memory a query needs (its score row and its codes), reserved up
 //    front from the server's budget, so admission is by device memory;
