@@ -126,3 +126,20 @@ def test_batch_device_graph_replay():
                 assert np.array_equal(d_ti[i].cpu().numpy().astype(np.uint64), eti)
         prof = sw.sw_db_get_profile(db)
         assert prof["phases"]["batch"]["calls"] == 3
+
+
+@pytest.mark.parametrize("A", [3, 32])
+def test_batch_alphabets_and_rows_per_thread_groups(A):
+    """Batches over alphabets of 3 and 32 codes (the query-pair profile holds A + 1 code
+    rows), with lengths spread so the pairs fall into several rows-per-thread groups (one
+    launch each); every score and top-k list must equal the oracle's."""
+    rng = np.random.default_rng(220 + A)
+    lengths = synth.gen_lengths(1200, synth.db_qtable(), 221, 1).astype(np.uint64)
+    res = rng.integers(0, A, size=int(lengths.sum())).astype(np.uint8)
+    off = np.zeros(lengths.size + 1, np.uint64)
+    off[1:] = np.cumsum(lengths)
+    M = rng.integers(-5, 6, size=(A, A)).astype(np.int8)
+    lens = [40, 41, 60, 64, 100, 128, 129, 150, 160, 161, 250, 300, 383, 384, 700, 960]
+    qs = [rng.integers(0, A, size=n).astype(np.uint8) for n in lens]
+    with sw.sw_db_load(res, off, alphabet=A) as db:
+        _check_batch(db, res, off, qs, M, 1, 6, 10)

@@ -129,3 +129,23 @@ def test_admission_by_device_budget(database):
         with pytest.raises(sw.SwError) as e:
             sw.sw_server_create(db, device_budget=slot // 2)
         assert e.value.status == "SW_ERR_OOM"
+
+
+def test_alphabet_32_alone_and_paired():
+    """A 32-code alphabet (the single-query ring then runs with a one-column skew): queries
+    of equal and of very different lengths through the server, paired or alone, must get
+    the oracle's top-k."""
+    rng = np.random.default_rng(331)
+    lengths = synth.gen_lengths(2000, synth.db_qtable(), 332, 1).astype(np.uint64)
+    res = rng.integers(0, 32, size=int(lengths.sum())).astype(np.uint8)
+    off = np.zeros(lengths.size + 1, np.uint64)
+    off[1:] = np.cumsum(lengths)
+    M = rng.integers(-4, 6, size=(32, 32)).astype(np.int8)
+    qs = [rng.integers(0, 32, size=n).astype(np.uint8) for n in (300, 300, 290, 40, 1200, 77)]
+    with sw.sw_db_load(res, off, alphabet=32) as db, \
+            sw.sw_server_create(db, max_active=6, slices=4) as srv:
+        tickets = [srv.submit(q, M, 1, 9, 10) for q in qs]
+        got = [srv.wait(t) for t in tickets]
+    for q, g in zip(qs, got):
+        ets, eti = _expect(res, off, q, 1, 9, 10, M)
+        assert np.array_equal(g[0], ets) and np.array_equal(g[1], eti), q.size
