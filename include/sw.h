@@ -294,6 +294,9 @@ typedef struct {
     uint64_t cells;            /* DP cells of the completed queries */
     double busy_ms;            /* wall time spent in waves */
     uint32_t pending, active, max_active, slices;
+    double gpu_ms;             /* device time of the waves (first to last command of each wave);
+                                  busy_ms - gpu_ms is the host's share: launches, the
+                                  wave-end synchronisation and bookkeeping */
 } sw_server_stats;
 
 /* Create a server (starts its scheduler thread). opts may be NULL. */
@@ -324,28 +327,41 @@ void sw_server_destroy(sw_server* srv);
  * one allocates): the caller passes everything as DEVICE buffers.
  *
  *   d_query    : DEVICE, qlen codes;  d_matrix : DEVICE, alphabet * alphabet int8
- *   d_residues : DEVICE, the database sequences concatenated (codes < 32)
+ *   d_residues : DEVICE, the database sequences concatenated (codes < alphabet)
  *   d_offsets  : DEVICE, n_seqs + 1 uint64 offsets into d_residues
  *   max_len    : HOST value, the longest sequence in the set
  *   d_scores   : DEVICE, n_seqs int32, written in database order
  *   stream     : cudaStream_t as void*; the work is enqueued there
  *
- * Scores are the exact int32 scores of recurrence (1), identical to
- * sw_search's. The working memory is one fixed device array of 33,554,688
- * bytes (32 MiB + 256 B) inside the library, held by every GPU that loads the
- * library until the process exits. It bounds the input: when qlen > 512,
- * every sequence must be at most 2048 residues (a larger max_len is rejected
- * with SW_ERR_INVALID_ARG; a sequence that breaks the promise gets score -1).
- * Queries of at most 512 residues take sequences of any length.
+ * For valid input the scores are identical to sw_search's on the same
+ * sequences. Inputs the kernel cannot score are marked in the output instead
+ * of failing the call (the host never reads the device buffers):
+ *   -1  the sequence is longer than 2048 residues while qlen > 512 (the
+ *       caller's max_len understated it);
+ *   -2  the sequence holds a code >= alphabet, or the query does (then every
+ *       score is -2). sw_search instead rejects such codes when the database
+ *       is loaded.
  *
- * The first call on each device looks up the array's device address with
- * cudaGetSymbolAddress (that device must be current) and caches it; make that
- * first call before any stream capture. All calls share the array and leave
- * their contents in it: the work counter is cleared at the start of every
- * call, but calls whose work overlaps on the GPU (different streams, or
- * different host threads, at the same time) race and give wrong scores.
- * Serialise them, e.g. on one stream. The call never calls cudaMalloc,
- * cudaFree or any allocating routine.
+ * The working memory is one fixed device array of 33,554,688 bytes (32 MiB +
+ * 256 B) inside the library, held by every GPU that loads the library until
+ * the process exits. It bounds the input: when qlen > 512, every sequence must
+ * be at most 2048 residues (a larger max_len is rejected with
+ * SW_ERR_INVALID_ARG). Queries of at most 512 residues take sequences of any
+ * length and use every SM; longer ones run on 128 blocks, one per row slot of
+ * the array.
+ *
+ * Every call looks up the array's device address with cudaGetSymbolAddress
+ * (with the caller's device current; nothing is cached, so a device reset is
+ * harmless). With lazy module loading (the CUDA default) the first call on a
+ * device is also when the library's module is loaded and the array and the
+ * module's code take their device memory: a caller that will later give all
+ * free memory to its own allocator should make one call before that, or run
+ * with CUDA_MODULE_LOADING=EAGER. Make that first call before any stream
+ * capture. All calls share the array and leave their contents in it: the work
+ * counter is cleared at the start of every call, but calls whose work overlaps
+ * on the GPU (different streams, or different host threads, at the same time)
+ * race and give wrong scores. Serialise them, e.g. on one stream. The call
+ * never calls cudaMalloc, cudaFree or any allocating routine.
  */
 sw_status sw_search_noalloc(const uint8_t* d_query, uint32_t qlen, const int8_t* d_matrix,
                             uint32_t alphabet, int32_t alpha, int32_t beta,

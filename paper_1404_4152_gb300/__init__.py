@@ -83,7 +83,7 @@ class sw_server_stats(ctypes.Structure):
                 ("rejected", ctypes.c_uint64), ("cells", ctypes.c_uint64),
                 ("busy_ms", ctypes.c_double), ("pending", ctypes.c_uint32),
                 ("active", ctypes.c_uint32), ("max_active", ctypes.c_uint32),
-                ("slices", ctypes.c_uint32)]
+                ("slices", ctypes.c_uint32), ("gpu_ms", ctypes.c_double)]
 
 
 class sw_alignment(ctypes.Structure):
@@ -317,7 +317,9 @@ def sw_search_noalloc(d_query, qlen: int, d_matrix, alphabet: int, alpha: int, b
     whole device pool, or cannot afford cudaMalloc's synchronisation): every
     buffer is the caller's (torch tensors or raw device pointers), and the
     library's fixed 32 MiB scratch array does the rest. Calls that overlap on
-    the GPU share that array and race; run them one after another.
+    the GPU share that array and race; run them one after another. Scores the
+    kernel cannot compute are marked: -1 for a sequence longer than 2048 residues
+    when the query is longer than 512, -2 for a code outside the alphabet.
     """
 
     def addr(x):
