@@ -82,10 +82,17 @@ def parse_args():
     p.add_argument("--batch-seqs", type=int, default=1_000_000)
     p.add_argument("--batch-queries", type=int, default=256)
     p.add_argument("--serve-seqs", type=int, default=20_000_000)
-    p.add_argument("--serve-rates", default="1.0,10",
-                   help="comma-separated Poisson arrival rates (queries/s; 10 and above are past "
-                        "one GPU's capacity); empty skips serving")
-    p.add_argument("--serve-arrivals", type=int, default=16)
+    p.add_argument("--serve-rates", default="10,50,100,500",
+                   help="comma-separated Poisson arrival rates (queries/s), all past one GPU's "
+                        "capacity of ~2.5 q/s; empty skips them")
+    p.add_argument("--serve-arrivals", type=int, default=200, help="arrivals per overload rate")
+    p.add_argument("--serve-knee", default="0.5,1,2",
+                   help="arrival rates around one GPU's capacity (the latency knee); empty skips")
+    p.add_argument("--serve-knee-arrivals", type=int, default=64)
+    p.add_argument("--serve-slots", type=int, default=8,
+                   help="queries on the GPU at once (device-memory slots)")
+    p.add_argument("--serve-queue", type=int, default=16,
+                   help="waiting queries before arrivals are rejected")
     p.add_argument("--long-steps", type=int, default=2,
                    help="timed searches of the long-sequence workloads (scores x1 and x3; 0 skips)")
     p.add_argument("--align-top", type=int, default=10,
@@ -342,13 +349,66 @@ def run_traceback(args, sw, w, db, top_index, qlens):
             "top1_per_query_ms": {"gpu": gpu_top * 1e3, "cpu_oracle_1_core": cpu_secs * 1e3}}
 
 
-def run_served(args, sw, rank):
-    """Serving: a resident database of 20,000,000 sequences; Poisson arrivals of queries
-    (log-normal lengths, median 300); p50/p99 latency and sustained GCUPS per rate."""
+def _serve_rate(sw, db, n_res, rate, n_arrivals, seed, slots, queue):
+    """One Poisson stream of n_arrivals queries at `rate` q/s through a fresh server."""
     import threading
 
+    lens = synth.served_query_lengths(n_arrivals, seed)
+    qs = synth.make_queries(lens, seed)
+    arrive = synth.arrival_times(len(qs), rate, seed)
+    srv = sw.sw_server_create(db, max_active=slots, max_queue=queue, slices=8)
+    tickets = [None] * len(qs)
+    t0 = time.perf_counter()
+
+    def submitter():
+        for i, q in enumerate(qs):
+            d = arrive[i] - (time.perf_counter() - t0)
+            if d > 0:
+                time.sleep(d)
+            try:
+                tickets[i] = srv.submit(q, synth.BLOSUM62, 1, 11, 10)
+            except sw.SwError as e:
+                if e.status != "SW_ERR_BUSY":
+                    raise
+
+    th = threading.Thread(target=submitter)
+    th.start()
+    th.join()
+    lat, queued, service = [], [], []
+    cells = 0
+    for i, tk in enumerate(tickets):
+        if tk is None:
+            continue
+        _, _, l = srv.wait(tk)
+        lat.append(l["done_ms"] - l["submit_ms"])
+        queued.append(l["admit_ms"] - l["submit_ms"])
+        service.append(l["done_ms"] - l["admit_ms"])
+        cells += int(qs[i].size) * n_res
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    srv.destroy()
+    lat = np.array(lat) if lat else np.zeros(1)
+    return {"rate_qps": rate, "arrivals": len(qs), "completed": int(st["completed"]),
+            "rejected": int(st["rejected"]),
+            "p50_s": float(np.percentile(lat, 50)) / 1e3, "p99_s": float(np.percentile(lat, 99)) / 1e3,
+            "mean_queue_s": float(np.mean(queued)) / 1e3 if queued else None,
+            "mean_service_s": float(np.mean(service)) / 1e3 if service else None,
+            "sustained_gcups": cells / wall / 1e9,
+            "busy_gcups": cells / (st["busy_ms"] / 1e3) / 1e9 if st["busy_ms"] else None,
+            "waves": int(st["waves"]), "wave_ms_mean": st["busy_ms"] / max(1, st["waves"]),
+            "wave_host_ms_mean": (st["busy_ms"] - st["gpu_ms"]) / max(1, st["waves"]),
+            "wall_s": wall}
+
+
+def run_served(args, sw, rank):
+    """Serving: a resident database of 20,000,000 sequences; Poisson arrivals of queries
+    (log-normal lengths, median 300) at the overload rates (10-500 q/s, a fixed number of
+    arrivals each, bounded admission with rejections counted) and at the knee rates below one
+    GPU's capacity; p50/p99 latency (queueing and service), sustained and busy GCUPS per rate,
+    and the host's share of each wave (launches and the wave-end synchronisation)."""
     rates = [float(r) for r in args.serve_rates.split(",") if r.strip()]
-    if not rates:
+    knee = [float(r) for r in args.serve_knee.split(",") if r.strip()]
+    if not rates and not knee:
         return None
     res, off = synth.make_db(args.serve_seqs, 1407 + 1000 * rank)
     db = sw.sw_db_load(res, off, alphabet=20)
@@ -357,50 +417,15 @@ def run_served(args, sw, rank):
     n_res = int(off[-1])
     del res
     out = []
-    for ri, rate in enumerate(rates):
-        lens = synth.served_query_lengths(args.serve_arrivals, 1407 + ri)
-        qs = synth.make_queries(lens, 1407 + ri)
-        arrive = synth.arrival_times(len(qs), rate, 1407 + ri)
-        srv = sw.sw_server_create(db, max_active=32, slices=8)
-        tickets = [None] * len(qs)
-        rejected = [0]
-        t0 = time.perf_counter()
-
-        def submitter():
-            for i, q in enumerate(qs):
-                d = arrive[i] - (time.perf_counter() - t0)
-                if d > 0:
-                    time.sleep(d)
-                try:
-                    tickets[i] = srv.submit(q, synth.BLOSUM62, 1, 11, 10)
-                except sw.SwError:
-                    rejected[0] += 1
-
-        th = threading.Thread(target=submitter)
-        th.start()
-        th.join()
-        lat = []
-        cells = 0
-        for i, tk in enumerate(tickets):
-            if tk is None:
-                continue
-            _, _, l = srv.wait(tk)
-            lat.append(l["done_ms"] - l["submit_ms"])
-            cells += int(qs[i].size) * n_res
-        wall = time.perf_counter() - t0
-        st = srv.stats()
-        srv.destroy()
-        lat = np.array(lat)
-        out.append({"rate_qps": rate, "arrivals": len(qs), "completed": int(lat.size),
-                    "rejected": rejected[0], "p50_ms": float(np.percentile(lat, 50)),
-                    "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
-                    "sustained_gcups": cells / wall / 1e9,
-                    "busy_gcups": cells / (st["busy_ms"] / 1e3) / 1e9 if st["busy_ms"] else None,
-                    "waves": st["waves"]})
+    runs = [(r, args.serve_arrivals) for r in rates] + [(r, args.serve_knee_arrivals) for r in knee]
+    for ri, (rate, n_arr) in enumerate(runs):
+        out.append(_serve_rate(sw, db, n_res, rate, n_arr, 1407 + ri, args.serve_slots,
+                               args.serve_queue))
     db.free()
-    return {"workload": f"served_stream: {args.serve_seqs:,} resident sequences ({n_res / 1e9:.2f} G aa); "
-                        f"Poisson arrivals, query lengths log-normal median 300 [20, 5000]; "
-                        f"32 query slots, 8 slices",
+    return {"workload": f"served_stream: {args.serve_seqs:,} resident sequences "
+                        f"({n_res / 1e9:.2f} G aa); Poisson arrivals, query lengths log-normal "
+                        f"median 300 [20, 5000]; {args.serve_slots} query slots, queue bound "
+                        f"{args.serve_queue} (arrivals beyond it rejected), 8 slices per query",
             "rates": out}
 
 
@@ -457,6 +482,7 @@ def run_ours(args):
         # the scaling runs time the headline search (and its e2e) only; the batched,
         # served, long-sequence and traceback legs are single-GPU measurements
         args.batch_steps, args.serve_rates, args.long_steps, args.align_top = 0, "", 0, 0
+        args.serve_knee = ""
 
     w = build_workload(args, rank)
     db = sw.sw_db_load(w.residues, w.offsets, alphabet=20, device=local, flags=sw.SW_DB_FLAG_PROFILE)
@@ -600,7 +626,7 @@ def run_ours(args):
                "h2d_bytes_per_step": int(sum(qlens) + len(qlens) * w.matrix.size),
                "d2h_bytes_per_step": int(len(qlens) * (4 * n + 12 * k + 4))}
 
-    served = run_served(args, sw, rank) if args.serve_rates.strip() else None
+    served = run_served(args, sw, rank)
 
     batched = None
     if args.batch_steps > 0:

@@ -102,9 +102,11 @@ struct sw_server {
     uint64_t* h_top_i = nullptr;
     std::vector<uint32_t> slice_tile0;  // slices + 1 tile boundaries (multiples of 8)
 
+    cudaEvent_t ev_wave0 = nullptr, ev_wave1 = nullptr;  // device time of one wave
+
     // statistics
     uint64_t waves = 0, completed = 0, rejected = 0, cells = 0;
-    double busy_ms = 0;
+    double busy_ms = 0, gpu_ms = 0;
 };
 
 namespace {
@@ -124,6 +126,8 @@ void srv_release(sw_server* s) {
     s->allocs.clear();
     if (s->h_top_s) cudaFreeHost(s->h_top_s);
     if (s->h_top_i) cudaFreeHost(s->h_top_i);
+    if (s->ev_wave0) cudaEventDestroy(s->ev_wave0);
+    if (s->ev_wave1) cudaEventDestroy(s->ev_wave1);
     if (s->stream) cudaStreamDestroy(s->stream);
 }
 
@@ -186,9 +190,10 @@ sw_status launch_items(sw_server* s, KernelChoice kc, const std::vector<QueryPai
 // enough for the pair to cost less than the two alone (the pair runs the longer
 // one's rows for both); the others run alone in the mode that packs two database
 // sequences instead.
-sw_status run_wave(sw_server* s, std::vector<std::shared_ptr<Request>>& act) {
+sw_status run_wave(sw_server* s, std::vector<std::shared_ptr<Request>>& act, double* wave_gpu_ms) {
     sw_db* db = s->db;
     cudaError_t e;
+    *wave_gpu_ms = 0;
     std::vector<std::shared_ptr<Request>> order = act;
     std::stable_sort(order.begin(), order.end(), [](const auto& x, const auto& y) {
         if (x->next_slice != y->next_slice) return x->next_slice < y->next_slice;
@@ -219,6 +224,8 @@ sw_status run_wave(sw_server* s, std::vector<std::shared_ptr<Request>>& act) {
         *c0 = t0 / 8;
         *n = (t1 + 7) / 8 - t0 / 8;
     };
+    if ((e = cudaEventRecord(s->ev_wave0, s->stream)) != cudaSuccess)
+        return cuda_fail(e, "server: wave event");
     if ((e = cudaMemsetAsync(s->d_counters, 0, 64, s->stream)) != cudaSuccess)
         return cuda_fail(e, "server: counter reset");
     std::vector<QueryPair> pairs, singles;
@@ -305,8 +312,11 @@ sw_status run_wave(sw_server* s, std::vector<std::shared_ptr<Request>>& act) {
     uint32_t nflag = 0;
     if ((e = cudaMemcpyAsync(&nflag, s->d_counters + 3, 4, cudaMemcpyDeviceToHost, s->stream)) !=
             cudaSuccess ||
+        (e = cudaEventRecord(s->ev_wave1, s->stream)) != cudaSuccess ||
         (e = cudaStreamSynchronize(s->stream)) != cudaSuccess)
         return cuda_fail(e, "server: wave");
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, s->ev_wave0, s->ev_wave1) == cudaSuccess) *wave_gpu_ms = ms;
     if (nflag > s->flag_cap)
         return fail(SW_ERR_INTERNAL, "server: %u saturated pairs exceed the rescoring list (%u)",
                     nflag, s->flag_cap);
@@ -364,12 +374,14 @@ void worker_loop(sw_server* s) {
         std::vector<std::shared_ptr<Request>> act = s->active;
         lk.unlock();
         const double tw0 = now_ms(s);
-        const sw_status st = run_wave(s, act);
+        double wave_gpu_ms = 0;
+        const sw_status st = run_wave(s, act, &wave_gpu_ms);
         const std::string err = st ? std::string(sw_last_error()) : std::string();
         const double tw1 = now_ms(s);
         lk.lock();
         s->waves += 1;
         s->busy_ms += tw1 - tw0;
+        s->gpu_ms += wave_gpu_ms;
         for (auto& r : act) {
             if (r->state == kCancelled) {  // cancelled during the wave
                 s->free_slots.push_back(r->slot);
@@ -466,6 +478,8 @@ extern "C" sw_status sw_server_create(sw_db* db, const sw_server_opts* opts, sw_
     const uint64_t slots = (uint64_t)s->grid * (wavefront_block_threads() / 32) * (32 / kShortT);
     const uint32_t A = s->max_active;
     if ((e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaEventCreate(&s->ev_wave0)) != cudaSuccess ||
+        (e = cudaEventCreate(&s->ev_wave1)) != cudaSuccess ||
         (e = srv_alloc(s.get(), (void**)&s->d_scores, (size_t)A * db->n_seqs * 4)) != cudaSuccess ||
         (e = srv_alloc(s.get(), (void**)&s->d_queries, (size_t)A * s->max_qlen)) != cudaSuccess ||
         (e = srv_alloc(s.get(), (void**)&s->d_matrix, SW_MAX_ALPHABET * SW_MAX_ALPHABET)) !=
@@ -595,6 +609,7 @@ extern "C" sw_status sw_server_get_stats(sw_server* s, sw_server_stats* out) {
     out->active = (uint32_t)s->active.size();
     out->max_active = s->max_active;
     out->slices = s->slices;
+    out->gpu_ms = s->gpu_ms;
     return SW_OK;
 }
 
