@@ -99,6 +99,9 @@ def parse_args():
                    help="alignments (traceback) of this many top hits per query of the 20-query stream "
                         "(0 skips)")
     p.add_argument("--no-tune", action="store_true")
+    p.add_argument("--scaling", default="strong", choices=["strong", "weak"],
+                   help="N > 1: one database partitioned over the GPUs (strong) or one database "
+                        "per GPU (weak)")
     return p.parse_args()
 
 
@@ -186,23 +189,104 @@ def cpu_oracle_sample(w, seconds: float, threads: int):
     return cells / dt / 1e9, {"sequences": S, "residues": int(off[-1]), "cells": cells, "seconds": dt}
 
 
-def build_workload(args, rank):
-    return synth.query_stream(seed=1405 + 1000 * rank, n_seqs=args.n_seqs, n_queries=args.n_queries)
+def build_workload(args, rank, world):
+    """The 20-query stream. Strong scaling (N > 1, the default): every rank generates the
+    same 2,000,000-sequence database and keeps its shard (shard.partition: residues dealt
+    longest first to the least-loaded rank). Weak scaling: each rank its own database."""
+    if world > 1 and args.scaling == "strong":
+        import dataclasses
+
+        from paper_1404_4152_gb300 import shard
+
+        full = synth.query_stream(seed=1405, n_seqs=args.n_seqs, n_queries=args.n_queries)
+        gi = shard.partition(full.offsets, world)[rank]
+        sres, soff = shard.shard_arrays(full.residues, full.offsets, gi)
+        return dataclasses.replace(full, residues=sres, offsets=soff), full, gi
+    w = synth.query_stream(seed=1405 + 1000 * rank, n_seqs=args.n_seqs, n_queries=args.n_queries)
+    return w, None, None
 
 
-def workload_config(w, args, world):
+def workload_config(w, args, world, full=None):
+    db = full if full is not None else w
+    per_gpu = "" if full is not None else " per GPU"
     return {
         "workload": (f"query_stream: {len(w.queries)} queries of {min(q.size for q in w.queries)}.."
-                     f"{max(q.size for q in w.queries)} aa, one at a time, vs {w.n_seqs:,} "
-                     f"sequences ({w.db_residues / 1e6:.0f} M aa) per GPU; BLOSUM62, beta={w.beta}, "
-                     f"alpha={w.alpha}; every score + top-{w.top_k}"),
-        "global_batch": len(w.queries) * world,
+                     f"{max(q.size for q in w.queries)} aa, one at a time, vs {db.n_seqs:,} "
+                     f"sequences ({db.db_residues / 1e6:.0f} M aa){per_gpu}"
+                     + (f", sharded over {world} GPUs" if full is not None else "")
+                     + f"; BLOSUM62, beta={w.beta}, alpha={w.alpha}; every score + top-{w.top_k}"),
+        "global_batch": len(w.queries) * (1 if full is not None else world),
         "db_sequences_per_gpu": w.n_seqs,
         "db_residues_per_gpu": w.db_residues,
         "query_lengths": [int(q.size) for q in w.queries],
-        "parallelism": f"db-shard x{world}" if world > 1 else "single GPU",
-        "l2": "inputs larger than L2 (database resident in HBM, ~0.7 GB per GPU > 129 MB L2)",
+        "parallelism": (f"db-shard x{world} (one database partitioned)" if full is not None
+                        else f"db x{world} (one database per GPU)" if world > 1 else "single GPU"),
+        "l2": "inputs larger than L2 (database resident in HBM, ~0.7 GB > 129 MB L2)",
     }
+
+
+def compact_batched(b):
+    if not b:
+        return None
+    return {"gcups": round(b["value"], 1), "vs_plain": round(b.get("vs_plain", 0.0), 4),
+            "padded_frac": b.get("padded_frac"), "launches_per_batch": b.get("launches_per_batch"),
+            "ms_per_step": round(b["ms_per_step"], 1)}
+
+
+def compact_served(s):
+    if not s:
+        return None
+    cols = ["rate_qps", "arrivals", "completed", "rejected", "p50_s", "p99_s", "sustained_gcups",
+            "busy_gcups"]
+    rows = [[r[c] if not isinstance(r[c], float) else round(r[c], 3 if c.endswith("_s") else 1)
+             for c in cols] for r in s["rates"]]
+    return {"columns": cols, "rates": rows}
+
+
+def check_sharded_top_k(sw, w, full, shard_index, db, d_ts, d_ti, rank, world):
+    """After the timed region of a sharded run: every query's shard-local top-k mapped to
+    global indices and merged over the ranks (one all-gather each, the only exchange), and
+    on rank 0 compared with the single-GPU search of the whole database."""
+    from paper_1404_4152_gb300 import shard
+
+    k = w.top_k
+    ts_all, ti_all = d_ts.cpu().numpy(), d_ti.cpu().numpy()
+    merged = [shard.allgather_top_k(ts_all[i], shard.local_to_global(ti_all[i], shard_index), k)
+              for i in range(len(w.queries))]
+    if rank != 0:
+        return None
+    equal = 0
+    with sw.sw_db_load(full.residues, full.offsets, alphabet=20) as whole:
+        for i, q in enumerate(full.queries):
+            _, ts, ti, _ = sw.sw_search(whole, q, full.matrix, full.alpha, full.beta, k,
+                                        want_scores=False)
+            equal += int(np.array_equal(ts, merged[i][0]) and np.array_equal(ti, merged[i][1]))
+    return {"queries": len(full.queries), "merged_equal_to_single_gpu": equal,
+            "exchange": f"one all-gather of {k} (score, index) pairs per rank per query"}
+
+
+def batch_padding(qlens, tuning):
+    """Padded query rows of a batch under the library's plan rule (queries sorted by length
+    and paired, the pair running the longer query's rows for both; each pair on the rows per
+    thread of least measured cost; whole passes of 8 x R rows): computed rows / real rows - 1,
+    and the number of rows-per-thread groups (one persistent launch each)."""
+    Rs = [8, 12, 16, 20, 24]
+    ns = (tuning or {}).get("ns_per_row_residue", {}).get("query_pair") or [0.0] * 5
+    order = sorted(qlens, reverse=True)
+    computed, groups = 0, set()
+    for i in range(0, len(order), 2):
+        la = order[i]
+        lb = order[i + 1] if i + 1 < len(order) else 0
+
+        def cost(j):
+            R = Rs[j]
+            per_pass = ns[j] * 8 * R if ns[j] > 0 else 3.5 * R + 8.0
+            return -(-la // (8 * R)) * per_pass * (0.97 if ns[j] <= 0 and R == 16 else 1.0)
+
+        j = min(range(5), key=cost)
+        groups.add(Rs[j])
+        computed += 2 * (-(-la // (8 * Rs[j]))) * 8 * Rs[j]
+    return computed / max(1, sum(qlens)) - 1.0, len(groups)
 
 
 def run_batched(args, sw, torch, dev, rank):
@@ -211,11 +295,11 @@ def run_batched(args, sw, torch, dev, rank):
     pairs); GCUPS and the kernel-phase time."""
     w = synth.query_batch(seed=1406 + 1000 * rank, n_seqs=args.batch_seqs, n_queries=args.batch_queries)
     db = sw.sw_db_load(w.residues, w.offsets, alphabet=20, flags=sw.SW_DB_FLAG_PROFILE)
-    if not args.no_tune:
-        sw.sw_db_autotune(db, w.matrix, w.alpha, w.beta)
+    tuning = None if args.no_tune else sw.sw_db_autotune(db, w.matrix, w.alpha, w.beta)
     qlens = [int(q.size) for q in w.queries]
     qoff = np.concatenate([[0], np.cumsum(qlens)]).astype(np.uint64)
     nq, n, k = len(qlens), w.n_seqs, w.top_k
+    padded_frac, groups = batch_padding(qlens, tuning)
     d_q = torch.from_numpy(np.concatenate(w.queries)).to(dev)
     d_m = torch.from_numpy(w.matrix.copy()).to(dev)
     d_s = torch.empty((nq, n), dtype=torch.int32, device=dev)
@@ -244,7 +328,9 @@ def run_batched(args, sw, torch, dev, rank):
                         f"vs {n:,} sequences ({w.db_residues / 1e6:.0f} M aa), one graph-captured "
                         f"batch per step (a persistent launch per rows-per-thread group)",
             "value": cells / (ms / 1e3) / 1e9, "unit": "GCUPS", "steps": args.batch_steps,
-            "ms_per_step": ms / args.batch_steps, "gpu_launches": int(prof["launches"])}
+            "ms_per_step": ms / args.batch_steps, "gpu_launches": int(prof["launches"]),
+            "launches_per_batch": int(prof["launches"]) // max(1, args.batch_steps),
+            "wavefront_launches_per_batch": groups, "padded_frac": round(padded_frac, 4)}
 
 
 def run_long(args, sw, torch, dev, rank):
@@ -433,7 +519,7 @@ def run_reference(args):
     world, rank, _ = dist_info()
     if rank != 0:
         return 0
-    w = build_workload(args, 0)
+    w, _, _ = build_workload(args, 0, 1)
     threads = os.cpu_count() or 1
     budget = max(2.0, min(12.0, 150.0 / max(1, args.steps + args.warmup)))
     vals = []
@@ -484,7 +570,7 @@ def run_ours(args):
         args.batch_steps, args.serve_rates, args.long_steps, args.align_top = 0, "", 0, 0
         args.serve_knee = ""
 
-    w = build_workload(args, rank)
+    w, full, shard_index = build_workload(args, rank, world)
     db = sw.sw_db_load(w.residues, w.offsets, alphabet=20, device=local, flags=sw.SW_DB_FLAG_PROFILE)
     tuning = None if args.no_tune else sw.sw_db_autotune(db, w.matrix, w.alpha, w.beta)
     n = w.n_seqs
@@ -539,21 +625,16 @@ def run_ours(args):
     prof = sw.sw_db_get_profile(db)
 
     t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    res_all = torch.tensor([float(w.db_residues)], dtype=torch.float64, device=dev)
     merged = None
     if world > 1:
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        # the one exchange of a sharded search: every rank's top-k (global indices) merged
-        from paper_1404_4152_gb300 import shard
-
-        last = len(qlens) - 1
-        ms_, mi_ = shard.allgather_top_k(d_ts[last].cpu().numpy(),
-                                         d_ti[last].cpu().numpy().astype(np.uint64) + rank * n, k)
-        merged = {"query": last, "top_scores": ms_.tolist()[:3], "top_index": mi_.tolist()[:3]}
+        torch.distributed.all_reduce(res_all, op=torch.distributed.ReduceOp.SUM)
     ms_max = float(t.item())
-    cells_rank = sum(qlens) * w.db_residues * args.steps
-    cells_all = cells_rank * world
+    cells_all = sum(qlens) * int(res_all.item()) * args.steps
     value = cells_all / (ms_max / 1e3) / 1e9
-
+    if full is not None:
+        merged = check_sharded_top_k(sw, w, full, shard_index, db, d_ts, d_ti, rank, world)
     # per-query GCUPS (outside the timed region)
     per_query = []
     for i, L in enumerate(qlens):
@@ -650,19 +731,23 @@ def run_ours(args):
     line = {
         "metric": "GCUPS", "value": value, "unit": "GCUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "s16x2", "data": "synthetic",
-        "config": workload_config(w, args, world),
+        "scaling": "strong" if full is not None else "weak", "vs_baseline": None, "dtype": "s16x2",
+        "data": "synthetic",
+        "config": workload_config(w, args, world, full),
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
         "gpu_launches": int(prof["launches"]),
         "phases_ms": {p: ph[p]["ms"] for p in ph},
-        "batched": batched,
-        "served": served,
-        "long_sequences": long_seqs,
-        "traceback": traceback,
-        "sharded_top_k": merged,
         "tuning": tuning,
         "per_query": per_query,
         "context": {"paper_xeon_phi_gcups_max": PAPER_PHI_GCUPS_MAX},
+        "traceback": traceback,
+        "long_sequences": long_seqs,
+        "sharded_top_k": merged,
+        "batched_detail": batched,
+        "served_detail": served,
+        # the headline comparison last, compact, so the end of the line carries it
+        "batched": compact_batched(batched),
+        "served": compact_served(served),
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -48,9 +48,33 @@ def shard_arrays(residues, offsets, global_index):
     new_off = np.zeros(gi.size + 1, dtype=np.uint64)
     np.cumsum(lengths, out=new_off[1:])
     out = np.empty(int(new_off[-1]), dtype=np.uint8)
-    for k, s in enumerate(gi):
-        out[int(new_off[k]):int(new_off[k + 1])] = res[int(off[s]):int(off[s + 1])]
+    src = off[gi].tolist()
+    dst = new_off.tolist()
+    for k in range(gi.size):
+        out[dst[k]:dst[k + 1]] = res[src[k]:src[k] + (dst[k + 1] - dst[k])]
     return out, new_off
+
+
+def local_to_global(local_index, global_index):
+    """Map a shard's top-k indices (positions in its shard) to global database indices."""
+    gi = np.asarray(global_index, dtype=np.uint64)
+    return gi[np.asarray(local_index, dtype=np.int64)]
+
+
+def sharded_top_k(residues, offsets, queries, k: int, search_shard, rank: int, world: int,
+                  group=None):
+    """The whole sharded search of one database on this rank: take this rank's shard of
+    ``partition``, call ``search_shard(shard_residues, shard_offsets, queries, k)`` (which
+    returns per query the shard-local top-k scores and indices, ordered as stage (iv)
+    orders them), map the indices to global ones and merge over all ranks with one
+    all-gather per query. Returns the global top-k (scores, indices) of every query."""
+    gi = partition(offsets, world)[rank]
+    sres, soff = shard_arrays(residues, offsets, gi)
+    local = search_shard(sres, soff, queries, k)
+    merged = []
+    for ts, ti in local:
+        merged.append(allgather_top_k(ts, local_to_global(ti, gi), k, group=group))
+    return merged
 
 
 def merge_top_k(parts, k: int):

@@ -67,6 +67,55 @@ def _worker(rank, world, port, q):
     dist.destroy_process_group()
 
 
+def _sharded_worker(rank, world, port, q):
+    """The sharded search entry point (shard.sharded_top_k), the oracle standing in for
+    each rank's GPU search of its shard."""
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    w = synth.small_search()
+    n = 900
+    off = w.offsets[: n + 1]
+    res = w.residues[: int(off[-1])]
+    queries = [w.queries[0], synth.make_queries([37], 9)[0]]
+
+    def search_shard(sres, soff, qs, k):
+        out = []
+        for qq in qs:
+            local = oracle.scores(qq, sres, soff, w.matrix, w.alpha, w.beta, nthreads=2)
+            out.append(pins.ranked_top_k(local, k))
+        return out
+
+    merged = shard.sharded_top_k(res, off, queries, 10, search_shard, rank, world)
+    q.put((rank, [(ms.tolist(), mi.tolist()) for ms, mi in merged]))
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_sharded_search_equals_single_database_top_k(world):
+    import torch.multiprocessing as mp
+
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_sharded_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    out = [q.get(timeout=180) for _ in procs]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    w = synth.small_search()
+    off = w.offsets[:901]
+    res = w.residues[: int(off[-1])]
+    for qi, qq in enumerate([w.queries[0], synth.make_queries([37], 9)[0]]):
+        full = oracle.scores(qq, res, off, w.matrix, w.alpha, w.beta)
+        es, ei = pins.ranked_top_k(full, 10)
+        for rank, lists in out:
+            assert lists[qi][0] == es.tolist() and lists[qi][1] == ei.tolist(), (rank, qi)
+
+
 def test_two_rank_allgather_top_k():
     import torch.multiprocessing as mp
 
