@@ -339,10 +339,12 @@ def run_long(args, sw, torch, dev, rank):
     near-duplicates; the second run scales matrix and penalties by 3 so the planted pairs pass the
     16-bit range and are rescored in int32. GCUPS and the per-phase device time."""
     out = []
-    for scale in (1, 3):
-        w = synth.long_sequences(seed=1408 + 1000 * rank, scale=scale)
+    # (scale, long tail, block threshold): the workload, the same x3, and the variant with
+    # 64 sequences of 20,000-35,000 residues with the block route (automatic) and without
+    for scale, tail, bt in ((1, 0, 0), (3, 0, 0), (1, 64, 0), (1, 64, sw.SW_BLOCK_ROUTE_OFF)):
+        w = synth.long_sequences(seed=1408 + 1000 * rank, scale=scale, long_tail=tail)
         db = sw.sw_db_load(w.residues, w.offsets, alphabet=20, long_threshold=3000,
-                           flags=sw.SW_DB_FLAG_PROFILE)
+                           flags=sw.SW_DB_FLAG_PROFILE, block_threshold=bt)
         q = w.queries[0]
         n, k = w.n_seqs, w.top_k
         d_q = torch.from_numpy(q).to(dev)
@@ -375,7 +377,10 @@ def run_long(args, sw, torch, dev, rank):
         out.append({"workload": f"{w.name}: one {q.size}-residue query vs {n:,} sequences "
                                 f"({w.db_residues / 1e6:.0f} M aa, {info['n_long']:,} above 3,000), "
                                 f"{len(planted)} planted near-duplicates"
-                                + (", matrix and penalties x3" if scale > 1 else ""),
+                                + (", matrix and penalties x3" if scale > 1 else "")
+                                + (f", {tail} sequences of 20,000-35,000 aa" if tail else ""),
+                    "block_route": ({"threshold": info["block_threshold"],
+                                     "sequences": info["n_block"]} if info["n_block"] else None),
                     "value": cells / (ms / 1e3) / 1e9, "unit": "GCUPS", "steps": args.long_steps,
                     "ms_per_step": ms / args.long_steps,
                     "phases_ms": {p: v["ms"] / args.long_steps for p, v in prof["phases"].items()},

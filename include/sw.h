@@ -68,6 +68,13 @@ typedef struct {
     uint64_t device_budget;     /* cap on the bytes this handle may allocate on the device
                                    (0 = no cap); exceeding it gives SW_ERR_OOM */
     uint32_t flags;             /* SW_DB_FLAG_* */
+    uint32_t block_threshold;   /* sequences longer than this (and than long_threshold) are
+                                   scored by a whole block of 8 warps each, the multi-warp
+                                   wavefront of the intra-sequence model (Section III.C),
+                                   beside the warp-per-pair kernel, so one very long
+                                   sequence does not leave one warp working after the
+                                   others finish. 0 = automatic: max(4 * long_threshold,
+                                   total residues / (64 * SM count)); UINT32_MAX = never */
 } sw_db_opts;
 
 #define SW_DB_FLAG_FORCE_INT32 1u   /* skip the packed 16-bit kernels; everything in int32 */
@@ -85,6 +92,9 @@ typedef struct {
     uint32_t max_length;
     uint64_t n_long;             /* sequences above long_threshold */
     int device;
+    uint64_t n_block;            /* sorted positions scored by the block wavefront (whole
+                                    tiles of 8 that hold a sequence above block_threshold) */
+    uint32_t block_threshold;    /* the threshold in effect */
 } sw_db_info;
 
 /* Per-call statistics (optional output of the search calls). */

@@ -47,14 +47,16 @@ class SwError(RuntimeError):
 
 class sw_db_opts(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("long_threshold", ctypes.c_uint32),
-                ("device_budget", ctypes.c_uint64), ("flags", ctypes.c_uint32)]
+                ("device_budget", ctypes.c_uint64), ("flags", ctypes.c_uint32),
+                ("block_threshold", ctypes.c_uint32)]
 
 
 class sw_db_info(ctypes.Structure):
     _fields_ = [("n_seqs", ctypes.c_uint64), ("total_residues", ctypes.c_uint64),
                 ("device_bytes", ctypes.c_uint64), ("alphabet", ctypes.c_uint32),
                 ("max_length", ctypes.c_uint32), ("n_long", ctypes.c_uint64),
-                ("device", ctypes.c_int)]
+                ("device", ctypes.c_int), ("n_block", ctypes.c_uint64),
+                ("block_threshold", ctypes.c_uint32)]
 
 
 class sw_stats(ctypes.Structure):
@@ -193,13 +195,18 @@ class Database:
         self.free()
 
 
+SW_BLOCK_ROUTE_OFF = 0xFFFFFFFF  # block_threshold: never use the block-wavefront route
+
+
 def sw_db_load(residues, offsets, alphabet: int = 20, device: int = 0, long_threshold: int = 0,
-               device_budget: int = 0, flags: int = 0) -> Database:
-    """Load database sequences (uint8 codes, uint64 offsets of n+1 entries) onto the GPU."""
+               device_budget: int = 0, flags: int = 0, block_threshold: int = 0) -> Database:
+    """Load database sequences (uint8 codes, uint64 offsets of n+1 entries) onto the GPU.
+    Sequences above ``block_threshold`` (0 = automatic, SW_BLOCK_ROUTE_OFF = never) are
+    scored by a block of 8 warps each beside the warp-per-pair kernel."""
     lib = load_library()
     res = np.ascontiguousarray(residues, dtype=np.uint8)
     off = np.ascontiguousarray(offsets, dtype=np.uint64)
-    opts = sw_db_opts(device, long_threshold, device_budget, flags)
+    opts = sw_db_opts(device, long_threshold, device_budget, flags, block_threshold)
     h = ctypes.c_void_p()
     _check(lib.sw_db_load(_ptr(res), _ptr(off), off.size - 1, alphabet, ctypes.byref(opts),
                           ctypes.byref(h)))
@@ -215,9 +222,10 @@ def sw_db_save(db: Database, path: str):
     _check(load_library().sw_db_save(db.handle, str(path).encode()))
 
 
-def sw_db_open(path: str, device: int = 0, device_budget: int = 0, flags: int = 0) -> Database:
+def sw_db_open(path: str, device: int = 0, device_budget: int = 0, flags: int = 0,
+               block_threshold: int = 0) -> Database:
     """Open a database written by sw_db_save (no sorting or tiling)."""
-    opts = sw_db_opts(device, 0, device_budget, flags)
+    opts = sw_db_opts(device, 0, device_budget, flags, block_threshold)
     h = ctypes.c_void_p()
     _check(load_library().sw_db_open(str(path).encode(), ctypes.byref(opts), ctypes.byref(h)))
     db = Database(h, 0, 0)

@@ -109,6 +109,9 @@ void release(sw_db* db) {
     db->allocs.clear();
     if (db->stream) cudaStreamDestroy(db->stream);
     if (db->a_stream) cudaStreamDestroy(db->a_stream);
+    if (db->blk_stream) cudaStreamDestroy(db->blk_stream);
+    if (db->blk_fork) cudaEventDestroy(db->blk_fork);
+    if (db->blk_join) cudaEventDestroy(db->blk_join);
     if (db->a_ev0) cudaEventDestroy(db->a_ev0);
     if (db->a_ev1) cudaEventDestroy(db->a_ev1);
     if (db->ev_t0) cudaEventDestroy(db->ev_t0);
@@ -240,6 +243,7 @@ extern "C" sw_status sw_db_load(const uint8_t* residues, const uint64_t* offsets
     db->max_len_long = db->n_long_tiles ? tile_len[0] : 0;
     db->max_len_short = db->n_long_tiles < n_tiles ? tile_len[db->n_long_tiles] : 0;
     db->tile_len_host = tile_len;
+    set_block_route(db, opts ? opts->block_threshold : 0);
 
     // device copies
     sw_status st = SW_OK;
@@ -334,6 +338,8 @@ extern "C" sw_status sw_db_get_info(const sw_db* db, sw_db_info* info) {
     info->max_length = db->max_len;
     info->n_long = db->n_long;
     info->device = db->device;
+    info->n_block = std::min<uint64_t>(db->n_block_tiles * kTileSeqs, db->n_seqs);
+    info->block_threshold = db->block_threshold;
     return SW_OK;
 }
 
@@ -499,6 +505,7 @@ extern "C" sw_status sw_db_open(const char* path, const sw_db_opts* opts, sw_db*
     cudaDeviceProp prop;
     cudaGetDeviceProperties(&prop, db->device);
     db->nsm = prop.multiProcessorCount;
+    set_block_route(db, opts ? opts->block_threshold : 0);
     sw_status st;
     if ((st = db_alloc(db, (void**)&db->d_misc, 64, "sw_db_open: counters")) ||
         (st = db_alloc(db, (void**)&db->d_tile_data, db->tile_bytes, "sw_db_open: tiles")) ||

@@ -48,6 +48,10 @@ struct sw_db {
     uint64_t total_residues = 0;
     uint32_t max_len = 0;
     uint32_t long_threshold = 3000;
+    uint32_t block_threshold = 0;   // in effect (resolved from the option)
+    uint64_t n_block_tiles = 0;     // tiles [0, n_block_tiles) go to the block wavefront
+    cudaStream_t blk_stream = nullptr;  // the block wavefront beside the search kernel
+    cudaEvent_t blk_fork = nullptr, blk_join = nullptr;
     uint64_t budget = 0;
     uint64_t dev_bytes = 0;
     uint32_t flags = 0;
@@ -156,6 +160,9 @@ int choose_pair_R(const sw_db* db, const std::vector<uint32_t>& lengths);
 // Whether queries of la >= lb rows cost less paired in the query-pair kernel than each
 // alone in the kernel `alone`.
 bool pair_pays(const sw_db* db, uint32_t la, uint32_t lb, swgb::KernelChoice alone);
+// Resolve the block-wavefront route from the option (0 = automatic, UINT32_MAX = never):
+// the long tiles whose longest sequence exceeds the threshold (sw_search.cu).
+void set_block_route(sw_db* db, uint32_t opt_threshold);
 // Allocate the per-handle search scratch (boundary rows, counters, top-k).
 sw_status sw_db_prepare_search(sw_db* db);
 sw_status ensure(sw_db* db, DevBuf& b, size_t bytes, const char* what);

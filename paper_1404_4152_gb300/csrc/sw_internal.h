@@ -148,6 +148,10 @@ struct RescoreArgs {
     uint64_t bstride;
     uint32_t* work_counter;
     uint32_t* dbg;                  // error word of the bounds-checked build (may be NULL)
+    // dense_n > 0: no list; entry e (< dense_count) is (query row e / dense_n, sorted
+    // position e % dense_n) -- every query against the first dense_n sorted positions
+    uint32_t dense_n;
+    uint32_t dense_count;
 };
 cudaError_t launch_rescore(const RescoreArgs& a, int grid, cudaStream_t stream);
 int rescore_blocks_per_sm(uint32_t alphabet);  // resident blocks per SM for this alphabet

@@ -1,5 +1,6 @@
 // Exact int32 rescoring of (query, database sequence) pairs whose 16-bit
-// lanes reached the saturation threshold.
+// lanes reached the saturation threshold, and int32 scoring of the very long
+// database sequences (the block route of the search, dense entries).
 //
 // The paper keeps scores exact by computing in 32-bit lanes throughout
 // (Section III); the packed 16-bit kernels here are exact below a threshold
@@ -22,14 +23,14 @@ __global__ void __launch_bounds__(bw::kThreads) rescore_kernel(const RescoreArgs
     bw::setup(smem, a.matrix, a.alphabet);
     uint32_t* const entry_s = reinterpret_cast<uint32_t*>(smem + bw::kOffRed + 3 * 4 * bw::kWarps);
     uint2* const row7 = a.boundary + (uint64_t)blockIdx.x * a.bstride;  // warp 7 -> warp 0
-    const uint32_t count = min(*a.count, a.cap);
+    const uint32_t count = a.dense_n ? a.dense_count : min(*a.count, a.cap);
     for (;;) {
         __syncthreads();  // the previous pair is finished with the shared state
         if (threadIdx.x == 0) *entry_s = atomicAdd(a.work_counter, 1u);
         __syncthreads();
         const uint32_t e = *entry_s;
         if (e >= count) break;
-        const uint2 ent = a.list[e];
+        const uint2 ent = a.dense_n ? make_uint2(e / a.dense_n, e % a.dense_n) : a.list[e];
         const uint32_t q = ent.x;
         const uint64_t sp = ent.y;
         const uint8_t* qs = a.qoff ? a.query + a.qoff[q] : a.query;

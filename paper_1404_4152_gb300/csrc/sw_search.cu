@@ -31,6 +31,7 @@ namespace {
 
 constexpr int kTopkBlocks = 256;
 constexpr uint64_t kRescoreScratch = 256ull << 20;
+constexpr int kBlockRouteCounter = 4;  // d_counters word of the block route's work counter
 
 const int kShortR[] = {8, 12, 16, 20, 24};
 
@@ -175,8 +176,27 @@ sw_status ensure(sw_db* db, DevBuf& b, size_t bytes, const char* what) {
     return SW_OK;
 }
 
+void set_block_route(sw_db* db, uint32_t opt_threshold) {
+    uint64_t t = opt_threshold;
+    if (t == 0)  // automatic: past what one warp-per-pair unit can take without a tail
+        t = std::max<uint64_t>(4ull * db->long_threshold,
+                               db->total_residues / (64ull * (uint64_t)std::max(db->nsm, 1)));
+    t = std::max<uint64_t>(t, db->long_threshold);
+    db->block_threshold = (uint32_t)std::min<uint64_t>(t, 0xffffffffu);
+    uint64_t n = 0;  // sequences above it: the first n sorted positions
+    for (uint32_t L : db->seq_len) n += L > db->block_threshold;
+    db->n_block_tiles = std::min<uint64_t>((n + kTileSeqs - 1) / kTileSeqs, db->n_long_tiles);
+}
+
 sw_status sw_db_prepare_search(sw_db* db) {
     sw_status st;
+    {
+        cudaError_t e;
+        if ((e = cudaStreamCreateWithFlags(&db->blk_stream, cudaStreamNonBlocking)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&db->blk_fork, cudaEventDisableTiming)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&db->blk_join, cudaEventDisableTiming)) != cudaSuccess)
+            return cuda_fail(e, "block-wavefront stream");
+    }
     if ((st = db_alloc(db, (void**)&db->d_counters, 256, "search counters"))) return st;
     if (cudaMemset(db->d_counters, 0, 256) != cudaSuccess)  // includes the error word
         return fail(SW_ERR_CUDA, "search counters: memset failed");
@@ -275,8 +295,9 @@ WavefrontArgs base_args(sw_db* db, const int8_t* d_matrix, int32_t alpha, int32_
     a.beta = beta;
     a.scores = d_scores;
     a.score_stride = stride;
-    a.bin[0].first_unit = 0;
-    a.bin[0].n_units = db->n_long_tiles * units_per_tile;
+    // tiles [0, n_block_tiles) are the block wavefront's (fork_block_route)
+    a.bin[0].first_unit = db->n_block_tiles * units_per_tile;
+    a.bin[0].n_units = (db->n_long_tiles - db->n_block_tiles) * units_per_tile;
     a.bin[0].boundary = db->d_bnd_long;
     a.bin[0].bstride = db->bstride_long;
     a.bin[1].first_unit = db->n_long_tiles * units_per_tile;
@@ -310,6 +331,39 @@ RescoreArgs rescore_args(sw_db* db, const int8_t* d_matrix, int32_t alpha, int32
     return r;
 }
 
+// The sequences of the block route (the very long ones: whole tiles at the front of the
+// sorted order) for nq queries: one block of 8 warps per (query, sequence) running the
+// multi-warp wavefront of sw_blockwave.cuh in int32, on the handle's second stream beside
+// the search kernel; join_block_route makes `stream` wait for it. r carries the query
+// (single_qlen, or qoff / qlen per query row) and outputs.
+sw_status fork_block_route(sw_db* db, RescoreArgs r, uint32_t nq, cudaStream_t stream,
+                           bool* forked) {
+    *forked = false;
+    if (!db->n_block_tiles || nq == 0) return SW_OK;
+    const uint64_t n = db->n_block_tiles * kTileSeqs;
+    r.list = nullptr;
+    r.count = nullptr;
+    r.cap = 0;
+    r.dense_n = (uint32_t)n;
+    r.dense_count = (uint32_t)std::min<uint64_t>(n * nq, 0xffffffffu);
+    r.work_counter = db->d_counters + kBlockRouteCounter;
+    const int grid = (int)std::min<uint64_t>((uint64_t)db->grid_rescore, r.dense_count);
+    cudaError_t e;
+    if ((e = cudaEventRecord(db->blk_fork, stream)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(db->blk_stream, db->blk_fork, 0)) != cudaSuccess ||
+        (e = launch_rescore(r, grid, db->blk_stream)) != cudaSuccess ||
+        (e = cudaEventRecord(db->blk_join, db->blk_stream)) != cudaSuccess)
+        return cuda_fail(e, "search: block-wavefront route");
+    *forked = true;
+    return SW_OK;
+}
+
+sw_status join_block_route(sw_db* db, bool forked, cudaStream_t stream) {
+    if (!forked) return SW_OK;
+    cudaError_t e = cudaStreamWaitEvent(stream, db->blk_join, 0);
+    return e == cudaSuccess ? SW_OK : cuda_fail(e, "search: block-wavefront join");
+}
+
 int grid_for(const sw_db* db, const KernelChoice& kc) {
     const int occ = std::max(1, wavefront_occupancy(kc, nullptr));
     return std::max(1, std::min(db->grid_short, db->nsm * occ));
@@ -335,10 +389,17 @@ sw_status enqueue_search(sw_db* db, const uint8_t* d_query, uint32_t qlen, const
         a.flag_list = db->d_flags2;
         a.flag_cap = (uint32_t)std::min<uint64_t>(db->n_seqs, 0xffffffffu);
         PhaseTimer pt(db, 0, stream, (uint64_t)qlen * db->total_residues);
+        RescoreArgs rb = rescore_args(db, d_matrix, alpha, beta, d_scores, db->n_seqs);
+        rb.query = d_query;
+        rb.single_qlen = qlen;
+        bool forked = false;
+        sw_status st = fork_block_route(db, rb, 1, stream, &forked);
+        if (st) return st;
         if ((e = launch_wavefront(kc, a, grid_for(db, kc), stream)) != cudaSuccess)
             return cuda_fail(e, "search: wavefront kernel");
+        if ((st = join_block_route(db, forked, stream))) return st;
         pt.done();
-        db->launches += 1;
+        db->launches += 1 + (forked ? 1 : 0);
     }
     if (!i32) {
         RescoreArgs r = rescore_args(db, d_matrix, alpha, beta, d_scores, db->n_seqs);
@@ -471,6 +532,13 @@ sw_status launch_batch(sw_db* db, const BatchPlan& pl, const uint8_t* d_queries,
     a.query = d_queries;
     a.flag_list = (uint2*)db->b_flags.p;
     a.flag_cap = pl.flag_cap;
+    RescoreArgs rb = rescore_args(db, d_matrix, alpha, beta, d_scores, db->n_seqs);
+    rb.query = d_queries;
+    rb.qoff = (const uint64_t*)db->b_qoff.p;
+    rb.qlen = (const uint32_t*)db->b_qlen.p;
+    bool forked = false;
+    sw_status st = fork_block_route(db, rb, nq, stream, &forked);
+    if (st) return st;
     for (size_t g = 0; g < pl.group_R.size(); ++g) {  // one launch per rows-per-thread group
         const KernelChoice kc{KernelChoice::kQueryPair, pl.group_R[g]};
         a.pairs = (const QueryPair*)db->b_pairs.p + pl.group_first[g];
@@ -479,6 +547,7 @@ sw_status launch_batch(sw_db* db, const BatchPlan& pl, const uint8_t* d_queries,
         if ((e = launch_wavefront(kc, a, grid_for(db, kc), stream)) != cudaSuccess)
             return cuda_fail(e, "batch: wavefront kernel");
     }
+    if ((st = join_block_route(db, forked, stream))) return st;
     RescoreArgs r = rescore_args(db, d_matrix, alpha, beta, d_scores, db->n_seqs);
     r.list = (const uint2*)db->b_flags.p;
     r.cap = pl.flag_cap;
@@ -574,7 +643,8 @@ sw_status enqueue_batch(sw_db* db, uint32_t nq, const uint8_t* d_queries,
         g.qlen = pl.qlen;
         g.group_R = pl.group_R;
         g.group_first = pl.group_first;
-        g.kernels = (uint32_t)pl.group_R.size() + 1 + (top_k ? topk_launch_count() : 0);
+        g.kernels = (uint32_t)pl.group_R.size() + 1 + (top_k ? topk_launch_count() : 0) +
+                    (db->n_block_tiles ? 1 : 0);
     }
     PhaseTimer pt(db, 3, stream, pl.cells);
     if ((e = cudaGraphLaunch(g.exec, stream)) != cudaSuccess)

@@ -20,10 +20,13 @@
 //    next T*R rows of the query profile (Section III.B.2) in shared memory.
 //  - The integer ALU pipe is the bottleneck: every max, fused add-max and
 //    byte permute runs there (16x2 adds run on the FMA pipe). One cell pair
-//    costs 4.5 ALU instructions (three fused add-max, one max, half of a
-//    three-way running max) plus, for two database sequences, one permute
-//    that merges their two int8 scores; two queries share the database
-//    residue, so their profile entry is already the packed pair.
+//    costs 3.5 ALU instructions: H as one three-way max with the zero floor,
+//    E and F as one fused add-max each, and half of a three-way running max
+//    (the diagonal add and H - beta run on the FMA pipe). The three-input and
+//    fused forms occupy the ALU pipe two cycles per warp instruction, a plain
+//    two-input max one. The int8 query-profile mode adds one permute per row
+//    that merges the two database sequences' scores; two queries share the
+//    database residue, so their profile entry is already the packed pair.
 //  - The running maximum tracks x = H[i-1][j-1] + fsbt instead of H: E and F
 //    only carry values strictly below an earlier H (by beta, or as a chain of
 //    equal values ending at one), so the largest H of the matrix is

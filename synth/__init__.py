@@ -220,6 +220,7 @@ class Workload:
 # regenerated alone.
 _S_DB_LEN, _S_DB_RES, _S_Q_LEN, _S_Q_RES, _S_PLANT_POS, _S_PLANT_MUT = 1, 2, 3, 4, 5, 6
 _S_ARRIVAL = 7
+_S_TAIL_POS, _S_TAIL_LEN = 8, 9
 
 DB_MEAN, DB_SD, DB_LO, DB_HI = 350.0, 250.0, 10, 5000
 _qtable_cache: dict = {}
@@ -294,12 +295,16 @@ def arrival_times(n: int, rate_per_s: float, seed: int) -> np.ndarray:
 
 
 def long_sequences(seed: int = 1408, n_seqs: int = 100_000, n_planted: int = 1000,
-            scale: int = 1) -> Workload:
+            scale: int = 1, long_tail: int = 0) -> Workload:
     """A 5,478-residue query against 100,000 long-ish sequences (mean 2000, up to 35,000)
     with near-duplicates of the query (5% substitutions) planted at random positions.
 
     scale > 1 multiplies the matrix and both penalties by that integer; every score then
     scales exactly, which pushes the planted pairs past the 16-bit range.
+
+    long_tail > 0 also sets that many other sequences to lengths uniform in [20,000, 35,000]
+    (the log-normal alone stays below ~27,000 at this size; the paper's database reaches
+    36,805), the tail that one warp per pair would leave running after the rest.
     """
     mu = math.log(2000.0) - 0.642 ** 2 / 2.0
     qt = _qtable(mu, 0.642, 10, 35000)
@@ -308,11 +313,19 @@ def long_sequences(seed: int = 1408, n_seqs: int = 100_000, n_planted: int = 100
     pos = np.unique((draws(n_planted * 2, seed, _S_PLANT_POS) % np.uint64(n_seqs)).astype(np.int64))
     pos = pos[:n_planted]
     lengths[pos] = q.size
+    if long_tail:
+        cand = (draws(long_tail * 4 + 16, seed, _S_TAIL_POS) % np.uint64(n_seqs)).astype(np.int64)
+        cand = [int(c) for c in dict.fromkeys(cand.tolist()) if c not in set(pos.tolist())]
+        tail = np.array(cand[:long_tail], dtype=np.int64)
+        lengths[tail] = uniform_u32(tail.size, 20000, 35000, seed, _S_TAIL_LEN)
     res, off = gen_residues(lengths, seed, _S_DB_RES)
     for k, p in enumerate(pos):
         res[int(off[p]):int(off[p + 1])] = mutate(q, seed, _S_PLANT_MUT, k, 500)
     m = (BLOSUM62.astype(np.int32) * scale).astype(np.int8)
-    w = Workload(f"long_sequences{'_x3' if scale == 3 else f'_x{scale}' if scale > 1 else ''}", res, off,
-                 [q], m, 1 * scale, 11 * scale, 10)
+    name = "long_sequences" + ("_tail" if long_tail else "") + (
+        "_x3" if scale == 3 else f"_x{scale}" if scale > 1 else "")
+    w = Workload(name, res, off, [q], m, 1 * scale, 11 * scale, 10)
     w.notes["planted"] = pos
+    if long_tail:
+        w.notes["tail"] = tail
     return w

@@ -83,5 +83,12 @@ int main(int argc, char** argv) {
            n_top, (unsigned long long)top_i[0], top_s[0], sum, same, rejected, al.score,
            al.q_begin, al.q_end, al.d_begin, al.d_end, (int)al.ops_len, ops + al.ops_offset,
            (unsigned long long)stats.cells);
+    /* every score and the whole top-k list, one line each */
+    printf("scores=");
+    for (int s = 0; s < N; ++s) printf(s ? ",%d" : "%d", scores[s]);
+    printf("\ntop=");
+    for (uint32_t k = 0; k < n_top; ++k)
+        printf(k ? ",%d:%llu" : "%d:%llu", top_s[k], (unsigned long long)top_i[k]);
+    printf("\n");
     return 0;
 }

@@ -60,3 +60,7 @@ def test_client_agrees_with_the_oracle(tmp_path):
     assert int(kv["align_score"]) == e["score"] and kv["ops"] == e["ops"]
     assert kv["q"] == f"{e['q_begin']}-{e['q_end']}" and kv["d"] == f"{e['d_begin']}-{e['d_end']}"
     assert int(kv["cells"]) == 60 * int(off[-1])
+    # every score and every top-k entry, element by element
+    assert [int(v) for v in kv["scores"].split(",")] == es.tolist()
+    top = [tuple(int(x) for x in e.split(":")) for e in kv["top"].split(",")]
+    assert top == list(zip(ets.tolist(), eti.tolist()))
