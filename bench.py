@@ -54,15 +54,15 @@ ALU_OPS_PER_CELL = 3.5
 ALU_LANES_PER_CLK_SM = 64     # 32-bit lanes per clock per SM on the integer ALU pipe (4 x 16)
 S16X2_CELLS_PER_LANE = 2      # one 32-bit lane holds two 16-bit DP cells
 PAPER_PHI_GCUPS_MAX = 58.8    # SWAPHI InterSP, one Xeon Phi 5110P, TrEMBL (Section IV.A)
-# DRAM bytes per DP cell of the dominant search kernel, the score-profile ring at 24 rows
-# per thread (ncu dram__bytes_read + _write on a 600,000-sequence case;
-# profiles/search_kernel_ring_807x600k_ncu.md), valid for the kernel source whose sha256
-# starts with TRAFFIC_SOURCE.
-TRAFFIC_BYTES_PER_CELL = 0.0187
-TRAFFIC_SOURCE = "ed66652d0f60ff7b"
-# ALU instructions per row update of that kernel in the same capture (ALU-pipe instructions
-# over row updates: VIADDMNMX, VIMNMX3, PRMT, ISETP, LOP3, ...; the 807-row query's last
-# pass of 8 rows per thread included): the mix the kernel executes, against the 3.5 minimum
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant search kernel
+# per launch: the mean over the 20 launches of one step of the 20-query stream against
+# 2,000,000 sequences, every launch captured (ncu, one pass, full size). Valid for that
+# workload and the kernel source whose sha256 starts with TRAFFIC_SOURCE.
+TRAFFIC_BYTES_PER_LAUNCH = 18.81e9
+TRAFFIC_SOURCE = "a61900cdfdd889e2"
+# ALU-pipe work per row update of that kernel (sm__pipe_alu_cycles_active over row updates,
+# 8.12 cycles, in two-cycle instruction equivalents; an 807-residue query's launch): the mix
+# the kernel executes, against the 3.5 minimum
 ALU_OPS_PER_CELL_MEASURED = 4.06
 
 
@@ -339,10 +339,16 @@ def run_long(args, sw, torch, dev, rank):
     near-duplicates; the second run scales matrix and penalties by 3 so the planted pairs pass the
     16-bit range and are rescored in int32. GCUPS and the per-phase device time."""
     out = []
-    # (scale, long tail, block threshold): the workload, the same x3, and the variant with
-    # 64 sequences of 20,000-35,000 residues with the block route (automatic) and without
-    for scale, tail, bt in ((1, 0, 0), (3, 0, 0), (1, 64, 0), (1, 64, sw.SW_BLOCK_ROUTE_OFF)):
-        w = synth.long_sequences(seed=1408 + 1000 * rank, scale=scale, long_tail=tail)
+    # (scale, long tail, sequences, block threshold): the workload, the same x3, and the
+    # variant with 64 sequences of 20,000-35,000 residues, with the block route and without,
+    # at 100,000 sequences (where no pair unit outgrows a warp's share: the automatic
+    # threshold routes nothing, so the route is forced at 20,000) and at 10,000 (where the
+    # automatic threshold routes the tail)
+    off = sw.SW_BLOCK_ROUTE_OFF
+    for scale, tail, n, bt in ((1, 0, 100_000, 0), (3, 0, 100_000, 0), (1, 64, 100_000, 20_000),
+                               (1, 64, 100_000, off), (1, 64, 10_000, 0), (1, 64, 10_000, off)):
+        w = synth.long_sequences(seed=1408 + 1000 * rank, scale=scale, long_tail=tail, n_seqs=n,
+                                 n_planted=1000 * n // 100_000)
         db = sw.sw_db_load(w.residues, w.offsets, alphabet=20, long_threshold=3000,
                            flags=sw.SW_DB_FLAG_PROFILE, block_threshold=bt)
         q = w.queries[0]
@@ -374,7 +380,7 @@ def run_long(args, sw, torch, dev, rank):
         saturated = int((d_s.cpu().numpy()[planted] > 32767).sum())
         db.free()
         cells = q.size * w.db_residues * args.long_steps
-        out.append({"workload": f"{w.name}: one {q.size}-residue query vs {n:,} sequences "
+        out.append({"workload": f"{w.name}: one {q.size}-residue query vs {w.n_seqs:,} sequences "
                                 f"({w.db_residues / 1e6:.0f} M aa, {info['n_long']:,} above 3,000), "
                                 f"{len(planted)} planted near-duplicates"
                                 + (", matrix and penalties x3" if scale > 1 else "")
@@ -666,7 +672,9 @@ def run_ours(args):
 
     src = os.path.join(ROOT, "paper_1404_4152_gb300", "csrc", "sw_wavefront.cu")
     same_kernel = hashlib.sha256(open(src, "rb").read()).hexdigest().startswith(TRAFFIC_SOURCE)
-    traffic = TRAFFIC_BYTES_PER_CELL * cells_per_launch if same_kernel else None
+    default_workload = (args.n_seqs == 2_000_000 and args.n_queries == 20 and full is None
+                        and world == 1)
+    traffic = TRAFFIC_BYTES_PER_LAUNCH if same_kernel and default_workload else None
     roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "Gop/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "dram_gbs": traffic / (mean_ms / 1e3) / 1e9 if traffic else None,
@@ -701,14 +709,16 @@ def run_ours(args):
 
         e2e_step()
         barrier()
+        e2e_steps = max(1, min(args.steps, 5))  # the same metric; a few steps keep the run short
         t0 = time.perf_counter()
-        for _ in range(args.steps):
+        for _ in range(e2e_steps):
             e2e_step()
         t1 = time.perf_counter()
         tt = torch.tensor([t1 - t0], dtype=torch.float64, device=dev)
         if world > 1:
             torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        e2e = {"value": cells_all / float(tt.item()) / 1e9, "unit": "GCUPS",
+        e2e = {"value": cells_all / args.steps * e2e_steps / float(tt.item()) / 1e9, "unit": "GCUPS",
+               "steps": e2e_steps,
                "h2d_bytes_per_step": int(sum(qlens) + len(qlens) * w.matrix.size),
                "d2h_bytes_per_step": int(len(qlens) * (4 * n + 12 * k + 4))}
 

@@ -74,7 +74,9 @@ typedef struct {
                                    beside the warp-per-pair kernel, so one very long
                                    sequence does not leave one warp working after the
                                    others finish. 0 = automatic: max(4 * long_threshold,
-                                   total residues / (64 * SM count)); UINT32_MAX = never */
+                                   total residues / (32 * SM count)), the length at which a
+                                   pair unit outgrows one warp's share of the search;
+                                   UINT32_MAX = never */
 } sw_db_opts;
 
 #define SW_DB_FLAG_FORCE_INT32 1u   /* skip the packed 16-bit kernels; everything in int32 */

@@ -178,9 +178,10 @@ sw_status ensure(sw_db* db, DevBuf& b, size_t bytes, const char* what) {
 
 void set_block_route(sw_db* db, uint32_t opt_threshold) {
     uint64_t t = opt_threshold;
-    if (t == 0)  // automatic: past what one warp-per-pair unit can take without a tail
+    if (t == 0)  // automatic: a pair unit (2 x L residues) longer than one warp's share of
+                 // the search (total residues / (16 warps x SMs)) would finish after the rest
         t = std::max<uint64_t>(4ull * db->long_threshold,
-                               db->total_residues / (64ull * (uint64_t)std::max(db->nsm, 1)));
+                               db->total_residues / (32ull * (uint64_t)std::max(db->nsm, 1)));
     t = std::max<uint64_t>(t, db->long_threshold);
     db->block_threshold = (uint32_t)std::min<uint64_t>(t, 0xffffffffu);
     uint64_t n = 0;  // sequences above it: the first n sorted positions
