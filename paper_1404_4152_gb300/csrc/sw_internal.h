@@ -177,14 +177,15 @@ cudaError_t launch_build_tiles(const uint8_t* residues, const uint64_t* offsets,
 cudaError_t launch_max_code(const uint8_t* residues, uint64_t n, uint32_t* out,
                             cudaStream_t stream);
 
-// Top-k over nq score rows of length n (row q at scores + q * row_stride).
+// Top-k over nq score rows of length n (row q at scores + q * row_stride): one launch;
+// each block selects its slice's top-k, the last block of a row merges them.
+constexpr uint32_t kTopkCandidates = 8192;  // per row: blocks x k candidates at most
 struct TopkScratch {
-    uint32_t* hist;        // nq * 2048
-    uint32_t* state;       // nq * 8
-    uint32_t* block_eq;    // nq * topk_blocks
-    int32_t* cand_score;   // nq * kmax
-    uint32_t* cand_index;  // nq * kmax (uint32 indices; n < 2^32)
-    int blocks;
+    int32_t* cand_score;   // nq * kTopkCandidates
+    uint32_t* cand_index;  // nq * kTopkCandidates
+    uint32_t* cand_count;  // nq * blocks
+    uint32_t* done;        // nq: blocks of the row that have finished (cleared per launch)
+    int blocks;            // most blocks per row
 };
 size_t topk_scratch_bytes(uint32_t nq, uint32_t kmax, int blocks);
 void topk_scratch_carve(void* base, uint32_t nq, uint32_t kmax, int blocks, TopkScratch* s);

@@ -3,16 +3,21 @@
 // equal scores ordered by ascending database index, which makes the list
 // unique.
 //
-// Exact radix select over the non-negative int32 scores, then a sort of the
-// selected k:
-//   1. three histogram/select rounds over 11 + 11 + 10 bits find the k-th
-//      largest score thr and how many scores lie strictly above it;
-//   2. one pass collects every score > thr (fewer than k of them) and counts
-//      scores == thr per contiguous block; a second pass takes the first
-//      (k - #above) scores == thr in index order;
-//   3. one block sorts the k candidates by (score desc, index asc).
-// Every row of a batch (one row per query) is handled in the same launches
-// (grid.y = query).
+// One launch per call (grid = blocks x rows). Every block takes a contiguous
+// slice of its row and selects the slice's top-k exactly; the last block of the
+// row to finish (a per-row counter) merges the blocks' candidates and sorts the
+// result. The global top-k is contained in the union of the slices' top-k, and
+// both selections break ties by index the same way, so the merge is exact.
+//
+// Selection of the top kk of M elements (non-negative int32 scores, in index
+// order), by the whole block:
+//   1. three histogram/select rounds over 11 + 11 + 10 bits of the score find the
+//      kk-th largest score thr and how many scores must be taken at thr;
+//   2. one ordered pass keeps every score > thr and the first of the scores ==
+//      thr in index order, writing them in index order (a block-wide scan), so a
+//      row's candidates, block after block, are again in index order.
+// The merge runs the same selection over the candidates (held in shared
+// memory), then sorts the kk survivors by (score desc, index asc) (bitonic).
 #include <cuda_runtime.h>
 #include <cstdint>
 
@@ -23,11 +28,10 @@ namespace swgb {
 namespace {
 
 constexpr int kBins = 2048;
-constexpr int kHistThreads = 512;
-constexpr int kGatherThreads = 256;
-
-// state[q * 8 + ...]
-enum { ST_PREFIX = 0, ST_KREM = 1, ST_ABOVE = 2, ST_NCAND = 3, ST_K = 4 };
+constexpr int kThreads = 512;
+constexpr int kWarpsT = kThreads / 32;
+constexpr uint32_t kMaxK = 1024;
+constexpr uint32_t kMinSlice = 1024;  // elements per block at least
 
 __device__ __forceinline__ int digit_shift(int round) { return round == 0 ? 21 : (round == 1 ? 10 : 0); }
 __device__ __forceinline__ uint32_t digit_mask(int round) { return round == 2 ? 0x3ffu : 0x7ffu; }
@@ -36,242 +40,233 @@ __device__ __forceinline__ uint32_t high_mask(int round) {
     return round == 0 ? 0u : (round == 1 ? 0xffe00000u : 0xfffffc00u);
 }
 
-__global__ void topk_init(uint32_t* state, uint32_t* hist, uint64_t n, uint32_t k) {
-    const uint32_t q = blockIdx.x;
-    for (int i = threadIdx.x; i < kBins; i += blockDim.x) hist[(uint64_t)q * kBins + i] = 0;
-    if (threadIdx.x == 0) {
-        const uint32_t kk = (uint32_t)((uint64_t)k < n ? k : n);
-        state[q * 8 + ST_PREFIX] = 0;
-        state[q * 8 + ST_KREM] = kk;
-        state[q * 8 + ST_ABOVE] = 0;
-        state[q * 8 + ST_NCAND] = 0;
-        state[q * 8 + ST_K] = kk;
-    }
-}
+struct SelState {
+    uint32_t prefix;  // the bits of thr found so far
+    uint32_t krem;    // elements still to take at or below the prefix
+};
 
-__global__ void topk_hist(const int32_t* __restrict__ scores, uint64_t row_stride, uint64_t n,
-                          int round, const uint32_t* __restrict__ state, uint32_t* hist) {
-    __shared__ uint32_t h[kBins];
-    const uint32_t q = blockIdx.y;
-    if (state[q * 8 + ST_K] == 0) return;
-    for (int i = threadIdx.x; i < kBins; i += blockDim.x) h[i] = 0;
-    __syncthreads();
-    const uint32_t prefix = state[q * 8 + ST_PREFIX];
-    const uint32_t hm = high_mask(round), dm = digit_mask(round);
-    const int sh = digit_shift(round);
-    const int32_t* row = scores + (uint64_t)q * row_stride;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (uint64_t)gridDim.x * blockDim.x) {
-        const uint32_t x = (uint32_t)row[i];
-        if ((x & hm) == prefix) atomicAdd(&h[(x >> sh) & dm], 1u);
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < kBins; i += blockDim.x)
-        if (h[i]) atomicAdd(&hist[(uint64_t)q * kBins + i], h[i]);
-}
+struct TopkShared {
+    uint32_t hist[kBins];
+    uint32_t warp_cnt[2][kWarpsT];
+    SelState st;
+    uint32_t last;
+};
 
-// One warp per query: pick the digit holding the k_rem-th largest element.
-__global__ void topk_select(int round, uint32_t* state, uint32_t* hist) {
-    const uint32_t q = blockIdx.x;
-    const int lane = threadIdx.x;
-    uint32_t* H = hist + (uint64_t)q * kBins;
-    uint32_t* st = state + q * 8;
-    const uint32_t krem = st[ST_KREM];
-    if (st[ST_K] == 0) return;
-    const int nb = round == 2 ? 1024 : kBins;
-    const int per = nb / 32;
-    // lane l owns bins [nb - (l+1)*per, nb - l*per) (descending order of lanes)
-    const int hi = nb - lane * per;
-    uint32_t sum = 0;
-    for (int b = hi - per; b < hi; ++b) sum += H[b];
-    // exclusive prefix over lanes (lane 0 = highest bins)
-    uint32_t incl = sum;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += v;
-    }
-    const uint32_t excl = incl - sum;
-    const bool mine = excl < krem && incl >= krem;
-    const unsigned who = __ballot_sync(0xffffffffu, mine);
-    if (mine) {
-        uint32_t above = excl;
-        int d = hi - 1;
-        for (; d >= hi - per; --d) {
-            if (above + H[d] >= krem) break;
-            above += H[d];
-        }
-        st[ST_PREFIX] |= ((uint32_t)d) << digit_shift(round);
-        st[ST_KREM] = krem - above;
-        st[ST_ABOVE] += above;
-    }
-    (void)who;
-    __syncwarp();
-    // clear the histogram for the next round
-    for (int b = lane; b < kBins; b += 32) H[b] = 0;
-}
-
-// Pass 1: collect scores > thr; count scores == thr per contiguous chunk.
-__global__ void topk_gather_above(const int32_t* __restrict__ scores, uint64_t row_stride,
-                                  uint64_t n, uint32_t* state, uint32_t* block_eq,
-                                  int32_t* cand_score, uint32_t* cand_index, uint32_t kmax) {
-    const uint32_t q = blockIdx.y;
-    uint32_t* st = state + q * 8;
-    if (st[ST_K] == 0) return;
-    const uint32_t thr = st[ST_PREFIX];
-    const uint64_t chunk = (n + gridDim.x - 1) / gridDim.x;
-    const uint64_t b0 = (uint64_t)blockIdx.x * chunk;
-    const uint64_t b1 = b0 + chunk < n ? b0 + chunk : n;
-    const int32_t* row = scores + (uint64_t)q * row_stride;
-    uint32_t eq = 0;
-    for (uint64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
-        const uint32_t x = (uint32_t)row[i];
-        if (x > thr) {
-            const uint32_t c = atomicAdd(&st[ST_NCAND], 1u);
-            cand_score[(uint64_t)q * kmax + c] = (int32_t)x;
-            cand_index[(uint64_t)q * kmax + c] = (uint32_t)i;
-        }
-        eq += (x == thr);
-    }
-    __shared__ uint32_t red[kGatherThreads / 32];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) eq += __shfl_xor_sync(0xffffffffu, eq, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = eq;
+// Block-wide: the top kk of M elements (score(i), index(i)), i in index order, by
+// (score desc, index asc), written in index order to out_s / out_i. Every thread
+// calls it; it begins and ends with a barrier.
+template <class Score, class Index>
+__device__ void block_select(Score score, Index index, uint32_t M, uint32_t kk, TopkShared& sh,
+                             int32_t* out_s, uint32_t* out_i) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        uint32_t s = 0;
-        for (int w = 0; w < kGatherThreads / 32; ++w) s += red[w];
-        block_eq[(uint64_t)q * gridDim.x + blockIdx.x] = s;
-    }
-}
-
-// Pass 2: the first k_rem scores == thr in index order.
-__global__ void topk_gather_equal(const int32_t* __restrict__ scores, uint64_t row_stride,
-                                  uint64_t n, const uint32_t* state, const uint32_t* block_eq,
-                                  int32_t* cand_score, uint32_t* cand_index, uint32_t kmax) {
-    const uint32_t q = blockIdx.y;
-    const uint32_t* st = state + q * 8;
-    if (st[ST_K] == 0) return;
-    const uint32_t thr = st[ST_PREFIX];
-    const uint32_t need = st[ST_KREM];
-    const uint32_t above = st[ST_ABOVE];
-    __shared__ uint32_t s_base;
-    __shared__ uint32_t warp_cnt[kGatherThreads / 32];
-    if (threadIdx.x == 0) {
-        uint32_t b = 0;
-        for (uint32_t i = 0; i < blockIdx.x; ++i) b += block_eq[(uint64_t)q * gridDim.x + i];
-        s_base = b;
-    }
-    __syncthreads();
-    uint32_t base = s_base;
-    if (base >= need) return;
-    const uint64_t chunk = (n + gridDim.x - 1) / gridDim.x;
-    const uint64_t b0 = (uint64_t)blockIdx.x * chunk;
-    const uint64_t b1 = b0 + chunk < n ? b0 + chunk : n;
-    const int32_t* row = scores + (uint64_t)q * row_stride;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (uint64_t t0 = b0; t0 < b1; t0 += blockDim.x) {  // block-uniform loop
-        const uint64_t i = t0 + threadIdx.x;
-        const bool hit = i < b1 && (uint32_t)row[i] == thr;
-        const unsigned m = __ballot_sync(0xffffffffu, hit);
-        if (lane == 0) warp_cnt[warp] = __popc(m);
+    if (tid == 0) sh.st = SelState{0u, kk};
+    for (int round = 0; round < 3; ++round) {
+        for (int i = tid; i < kBins; i += kThreads) sh.hist[i] = 0;
         __syncthreads();
-        uint32_t before = base;
-        for (int w = 0; w < warp; ++w) before += warp_cnt[w];
-        before += __popc(m & ((1u << lane) - 1u));
-        if (hit && before < need) {
-            cand_score[(uint64_t)q * kmax + above + before] = (int32_t)thr;
-            cand_index[(uint64_t)q * kmax + above + before] = (uint32_t)i;
-        }
-        uint32_t tot = 0;
-        for (int w = 0; w < kGatherThreads / 32; ++w) tot += warp_cnt[w];
+        const uint32_t prefix = sh.st.prefix, hm = high_mask(round), dm = digit_mask(round);
+        const int shft = digit_shift(round);
+        if (kk > 0)
+            for (uint32_t i = tid; i < M; i += kThreads) {
+                const uint32_t x = score(i);
+                if ((x & hm) == prefix) atomicAdd(&sh.hist[(x >> shft) & dm], 1u);
+            }
         __syncthreads();
-        base += tot;
-        if (base >= need) break;
-    }
-}
-
-// One block per query sorts the k candidates (bitonic, padded to 1024).
-__global__ void topk_sort(const uint32_t* state, const int32_t* cand_score,
-                          const uint32_t* cand_index, uint32_t kmax, int32_t* top_scores,
-                          uint64_t* top_index, uint32_t k_out) {
-    __shared__ uint64_t key[1024];
-    const uint32_t q = blockIdx.x;
-    const uint32_t k = state[q * 8 + ST_K];
-    for (int i = threadIdx.x; i < 1024; i += blockDim.x) {
-        uint64_t v = 0;  // sorts last
-        if ((uint32_t)i < k) {
-            // descending score, ascending index: key = (score << 32) | ~index, sorted descending
-            const uint32_t s = (uint32_t)cand_score[(uint64_t)q * kmax + i];
-            const uint32_t idx = cand_index[(uint64_t)q * kmax + i];
-            v = ((uint64_t)(s + 1u) << 32) | (uint64_t)(~idx);
+        if (warp == 0 && kk > 0) {
+            // the digit holding the krem-th largest element: lane l sums bins
+            // [nb - (l+1) per, nb - l per), lanes in descending order of bins
+            const uint32_t krem = sh.st.krem;
+            const int nb = round == 2 ? 1024 : kBins;
+            const int per = nb / 32;
+            const int hi = nb - lane * per;
+            uint32_t sum = 0;
+            for (int b = hi - per; b < hi; ++b) sum += sh.hist[b];
+            uint32_t incl = sum;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += v;
+            }
+            const uint32_t excl = incl - sum;
+            if (excl < krem && incl >= krem) {  // exactly one lane
+                uint32_t above = excl;
+                int d = hi - 1;
+                for (; d >= hi - per; --d) {
+                    if (above + sh.hist[d] >= krem) break;
+                    above += sh.hist[d];
+                }
+                sh.st.prefix = prefix | ((uint32_t)d << shft);
+                sh.st.krem = krem - above;
+            }
         }
-        key[i] = v;
+        __syncthreads();
+    }
+    const uint32_t thr = sh.st.prefix;
+    const uint32_t need = kk > 0 ? sh.st.krem : 0;  // scores == thr to take, first in index order
+    // ordered pass: tiles of kThreads elements
+    uint32_t base_sel = 0, base_eq = 0;
+    for (uint32_t t0 = 0; kk > 0 && t0 < M; t0 += kThreads) {
+        const uint32_t i = t0 + tid;
+        const uint32_t x = i < M ? score(i) : 0u;
+        const bool gt = i < M && x > thr;
+        const bool eq = i < M && x == thr;
+        const unsigned meq = __ballot_sync(0xffffffffu, eq);
+        if (lane == 0) sh.warp_cnt[0][warp] = __popc(meq);
+        __syncthreads();
+        uint32_t eq_before = base_eq, eq_tile = 0;
+        for (int w = 0; w < kWarpsT; ++w) {
+            const uint32_t c = sh.warp_cnt[0][w];
+            if (w < warp) eq_before += c;
+            eq_tile += c;
+        }
+        eq_before += __popc(meq & ((1u << lane) - 1u));
+        const bool sel = gt || (eq && eq_before < need);
+        const unsigned msel = __ballot_sync(0xffffffffu, sel);
+        if (lane == 0) sh.warp_cnt[1][warp] = __popc(msel);
+        __syncthreads();
+        uint32_t sel_before = base_sel, sel_tile = 0;
+        for (int w = 0; w < kWarpsT; ++w) {
+            const uint32_t c = sh.warp_cnt[1][w];
+            if (w < warp) sel_before += c;
+            sel_tile += c;
+        }
+        sel_before += __popc(msel & ((1u << lane) - 1u));
+        if (sel && sel_before < kk) {
+            out_s[sel_before] = (int32_t)x;
+            out_i[sel_before] = index(i);
+        }
+        base_sel += sel_tile;
+        base_eq += eq_tile;
+        __syncthreads();  // warp_cnt is rewritten by the next tile
     }
     __syncthreads();
-    for (int size = 2; size <= 1024; size <<= 1) {
+}
+
+// grid = (blocks, rows). Dynamic shared memory: the row's candidates for the merge
+// (kTopkCandidates scores and indices) and the sort keys.
+__global__ void __launch_bounds__(kThreads) topk_kernel(const int32_t* __restrict__ scores,
+                                                        uint64_t row_stride, uint64_t n,
+                                                        uint32_t k, TopkScratch s,
+                                                        int32_t* top_scores, uint64_t* top_index,
+                                                        uint32_t k_out) {
+    extern __shared__ __align__(16) uint8_t dyn[];
+    __shared__ TopkShared sh;
+    int32_t* const m_s = reinterpret_cast<int32_t*>(dyn);
+    uint32_t* const m_i = reinterpret_cast<uint32_t*>(dyn + kTopkCandidates * 4);
+    uint64_t* const key = reinterpret_cast<uint64_t*>(dyn + kTopkCandidates * 8);
+    const uint32_t q = blockIdx.y, b = blockIdx.x, B = gridDim.x;
+    const int tid = threadIdx.x;
+    const int32_t* row = scores + (uint64_t)q * row_stride;
+
+    // ---- this block's slice ----
+    const uint64_t chunk = (n + B - 1) / B;
+    const uint64_t b0 = (uint64_t)b * chunk;
+    const uint64_t b1 = b0 + chunk < n ? b0 + chunk : n;
+    const uint32_t M = b1 > b0 ? (uint32_t)(b1 - b0) : 0u;
+    const uint32_t kk = M < k ? M : k;
+    int32_t* const cs = s.cand_score + (uint64_t)q * kTopkCandidates + (uint64_t)b * k;
+    uint32_t* const ci = s.cand_index + (uint64_t)q * kTopkCandidates + (uint64_t)b * k;
+    block_select([&](uint32_t i) { return (uint32_t)row[b0 + i]; },
+                 [&](uint32_t i) { return (uint32_t)(b0 + i); }, M, kk, sh, cs, ci);
+    if (tid == 0) s.cand_count[(uint64_t)q * s.blocks + b] = kk;
+
+    // ---- the last block of the row merges ----
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) sh.last = atomicAdd(&s.done[q], 1u) == B - 1;
+    __syncthreads();
+    if (!sh.last) return;
+    __threadfence();
+    // the candidates, block after block (index order), into shared memory
+    uint32_t total = 0;
+    for (uint32_t bb = 0; bb < B; ++bb) {
+        const uint32_t c = *reinterpret_cast<volatile const uint32_t*>(&s.cand_count[(uint64_t)q * s.blocks + bb]);
+        const volatile int32_t* src_s = s.cand_score + (uint64_t)q * kTopkCandidates + (uint64_t)bb * k;
+        const volatile uint32_t* src_i = s.cand_index + (uint64_t)q * kTopkCandidates + (uint64_t)bb * k;
+        for (uint32_t j = tid; j < c; j += kThreads) {
+            m_s[total + j] = src_s[j];
+            m_i[total + j] = src_i[j];
+        }
+        total += c;
+    }
+    const uint32_t kf = total < k ? total : k;  // = min(k, n)
+    // the selection writes its kk survivors over the front of the same arrays only after
+    // reading them all: select into the key area first
+    int32_t* const f_s = reinterpret_cast<int32_t*>(key);
+    uint32_t* const f_i = reinterpret_cast<uint32_t*>(key) + kMaxK;
+    block_select([&](uint32_t i) { return (uint32_t)m_s[i]; }, [&](uint32_t i) { return m_i[i]; },
+                 total, kf, sh, f_s, f_i);
+    // sort the kf survivors: key = (score + 1) << 32 | ~index, descending (pads sort last)
+    uint64_t mine[kMaxK / kThreads];
+#pragma unroll
+    for (int r = 0; r < (int)(kMaxK / kThreads); ++r) {
+        const uint32_t i = tid + r * kThreads;
+        mine[r] = i < kf ? (((uint64_t)((uint32_t)f_s[i] + 1u) << 32) | (uint64_t)(~f_i[i])) : 0ull;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < (int)(kMaxK / kThreads); ++r) key[tid + r * kThreads] = mine[r];
+    __syncthreads();
+    for (int size = 2; size <= (int)kMaxK; size <<= 1) {
         for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            for (int i = threadIdx.x; i < 1024; i += blockDim.x) {
+            for (int i = tid; i < (int)kMaxK; i += kThreads) {
                 const int j = i ^ stride;
                 if (j > i) {
                     const bool desc = (i & size) == 0;
-                    const uint64_t a = key[i], b = key[j];
-                    if (desc ? (a < b) : (a > b)) { key[i] = b; key[j] = a; }
+                    const uint64_t x = key[i], y = key[j];
+                    if (desc ? (x < y) : (x > y)) { key[i] = y; key[j] = x; }
                 }
             }
             __syncthreads();
         }
     }
-    for (uint32_t i = threadIdx.x; i < k; i += blockDim.x) {
+    for (uint32_t i = tid; i < kf; i += kThreads) {
         const uint64_t v = key[i];
         top_scores[(uint64_t)q * k_out + i] = (int32_t)((uint32_t)(v >> 32) - 1u);
         top_index[(uint64_t)q * k_out + i] = (uint64_t)(uint32_t)~(uint32_t)(v & 0xffffffffu);
     }
+    if (tid == 0) s.done[q] = 0;  // ready for the next launch
 }
+
+constexpr size_t kDynBytes = (size_t)kTopkCandidates * 8 + (size_t)kMaxK * 8;
 
 }  // namespace
 
 size_t topk_scratch_bytes(uint32_t nq, uint32_t kmax, int blocks) {
-    const size_t a = (size_t)nq * kBins * 4;
-    const size_t b = (size_t)nq * 8 * 4;
-    const size_t c = (size_t)nq * blocks * 4;
-    const size_t d = (size_t)nq * kmax * 4 * 2;
-    return a + b + c + d + 256;
+    (void)kmax;
+    return (size_t)nq * kTopkCandidates * 8 + (size_t)nq * blocks * 4 + (size_t)nq * 4 + 256;
 }
 
 void topk_scratch_carve(void* base, uint32_t nq, uint32_t kmax, int blocks, TopkScratch* s) {
+    (void)kmax;
     char* p = (char*)base;
-    s->hist = (uint32_t*)p; p += (size_t)nq * kBins * 4;
-    s->state = (uint32_t*)p; p += (size_t)nq * 8 * 4;
-    s->block_eq = (uint32_t*)p; p += (size_t)nq * blocks * 4;
-    s->cand_score = (int32_t*)p; p += (size_t)nq * kmax * 4;
-    s->cand_index = (uint32_t*)p;
+    s->cand_score = (int32_t*)p; p += (size_t)nq * kTopkCandidates * 4;
+    s->cand_index = (uint32_t*)p; p += (size_t)nq * kTopkCandidates * 4;
+    s->cand_count = (uint32_t*)p; p += (size_t)nq * blocks * 4;
+    s->done = (uint32_t*)p;
     s->blocks = blocks;
 }
 
-int topk_launch_count() { return 1 + 3 * 2 + 3; }
+int topk_launch_count() { return 1; }
 
 cudaError_t launch_topk(const int32_t* scores, uint64_t row_stride, uint64_t n, uint32_t nq,
                         uint32_t k, const TopkScratch& s, int32_t* top_scores,
                         uint64_t* top_index, cudaStream_t stream) {
     if (k == 0 || n == 0 || nq == 0) return cudaSuccess;
-    if (k > 1024) return cudaErrorInvalidValue;
-    topk_init<<<nq, 256, 0, stream>>>(s.state, s.hist, n, k);
-    const int hblocks = (int)((n + kHistThreads * 16 - 1) / (kHistThreads * 16));
-    const dim3 hg(hblocks < 1 ? 1 : (hblocks > 1024 ? 1024 : hblocks), nq);
-    for (int round = 0; round < 3; ++round) {
-        topk_hist<<<hg, kHistThreads, 0, stream>>>(scores, row_stride, n, round, s.state, s.hist);
-        topk_select<<<nq, 32, 0, stream>>>(round, s.state, s.hist);
-    }
-    const dim3 gg(s.blocks, nq);
-    topk_gather_above<<<gg, kGatherThreads, 0, stream>>>(scores, row_stride, n, s.state,
-                                                          s.block_eq, s.cand_score, s.cand_index,
-                                                          1024);
-    topk_gather_equal<<<gg, kGatherThreads, 0, stream>>>(scores, row_stride, n, s.state,
-                                                          s.block_eq, s.cand_score, s.cand_index,
-                                                          1024);
-    topk_sort<<<nq, 1024, 0, stream>>>(s.state, s.cand_score, s.cand_index, 1024, top_scores,
-                                       top_index, k);
+    if (k > kMaxK) return cudaErrorInvalidValue;
+    // blocks per row: every block's k candidates fit the row's candidate area, and every
+    // block has at least kMinSlice elements
+    uint64_t B = kTopkCandidates / k;
+    const uint64_t by_n = (n + kMinSlice - 1) / kMinSlice;
+    if (B > by_n) B = by_n;
+    if (B > (uint64_t)s.blocks) B = (uint64_t)s.blocks;
+    if (B < 1) B = 1;
+    cudaError_t e = cudaFuncSetAttribute(topk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kDynBytes);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(s.done, 0, (size_t)nq * 4, stream)) != cudaSuccess) return e;
+    topk_kernel<<<dim3((unsigned)B, nq), kThreads, kDynBytes, stream>>>(scores, row_stride, n, k, s,
+                                                                        top_scores, top_index, k);
     return cudaGetLastError();
 }
 

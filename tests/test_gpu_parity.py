@@ -147,6 +147,30 @@ def test_top_k_sizes_and_ties(k):
         _check(db, res, off, q, M, 1, 2, k)
 
 
+@pytest.mark.parametrize("k", [10, 1024])
+def test_top_k_ties_across_many_blocks(k):
+    """200,000 short sequences over a 2-letter alphabet: scores take a handful of values,
+    so the k-th score is tied thousands of times across the top-k kernel's blocks (each
+    selects its slice's top k, the row's last block merges) and the list must take the
+    lowest indices among the ties."""
+    rng = np.random.default_rng(k + 17)
+    A = 2
+    M = np.array([[1, -1], [-1, 1]], np.int8)
+    lengths = rng.integers(0, 12, size=200_000).astype(np.uint64)
+    res, off = _db_from_lengths(lengths, 92, A)
+    q = rng.integers(0, A, size=20).astype(np.uint8)
+    with sw.sw_db_load(res, off, alphabet=A) as db:
+        _check(db, res, off, q, M, 1, 2, k)
+        # a batch: every row its own top-k in the same launch
+        qs = [q, rng.integers(0, A, size=9).astype(np.uint8), rng.integers(0, A, size=31).astype(np.uint8)]
+        rows, ts, ti, nt, _ = sw.sw_search_batch(db, qs, M, 1, 2, k, want_scores=True)
+    for r, qq, a, b in zip(rows, qs, ts, ti):
+        es = oracle.scores(qq, res, off, M, 1, 2)
+        assert np.array_equal(r, es)
+        ets, eti = pins.ranked_top_k(es, k)
+        assert np.array_equal(a, ets) and np.array_equal(b, eti)
+
+
 def test_top_k_larger_than_database():
     lengths = [5, 9, 0, 14]
     res, off = _db_from_lengths(lengths, 3)
