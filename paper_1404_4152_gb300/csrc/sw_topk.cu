@@ -66,11 +66,18 @@ __device__ void block_select(Score score, Index index, uint32_t M, uint32_t kk, 
         __syncthreads();
         const uint32_t prefix = sh.st.prefix, hm = high_mask(round), dm = digit_mask(round);
         const int shft = digit_shift(round);
-        if (kk > 0)
-            for (uint32_t i = tid; i < M; i += kThreads) {
+        // scores cluster in a few bins (the upper digits of small scores are all zero):
+        // lanes of a warp that hit the same bin add their count with one atomic
+        for (uint32_t t0 = 0; kk > 0 && t0 < M; t0 += kThreads) {
+            const uint32_t i = t0 + tid;
+            uint32_t bin = 0xffffffffu;
+            if (i < M) {
                 const uint32_t x = score(i);
-                if ((x & hm) == prefix) atomicAdd(&sh.hist[(x >> shft) & dm], 1u);
+                if ((x & hm) == prefix) bin = (x >> shft) & dm;
             }
+            const unsigned same = __match_any_sync(0xffffffffu, bin);
+            if (bin != 0xffffffffu && lane == __ffs(same) - 1) atomicAdd(&sh.hist[bin], __popc(same));
+        }
         __syncthreads();
         if (warp == 0 && kk > 0) {
             // the digit holding the krem-th largest element: lane l sums bins
