@@ -61,6 +61,8 @@ def test_results_alone_and_in_a_mix(database):
         lat = got[i][2]
         assert lat["submit_ms"] <= lat["admit_ms"] <= lat["done_ms"]
     assert st["completed"] == len(qs) + 1 and st["waves"] >= 5
+    # the waves' device time is measured and lies within their wall time
+    assert 0 < st["gpu_ms"] <= st["busy_ms"] * 1.01 + 0.5
 
 
 def test_different_schemes_in_the_queue(database):

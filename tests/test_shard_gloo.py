@@ -135,3 +135,28 @@ def test_two_rank_allgather_top_k():
     es, ei = pins.ranked_top_k(full, 10)
     for rank, ms, mi in out:
         assert ms == es.tolist() and mi == ei.tolist(), rank
+
+
+def test_bench_strong_scaling_shards_partition_one_database():
+    """bench.py's strong-scaling workload: every rank draws the same database and keeps
+    its shard; the shards hold every sequence exactly once, residue for residue."""
+    import argparse
+
+    import bench
+
+    args = argparse.Namespace(scaling="strong", n_seqs=3000, n_queries=3)
+    world = 3
+    full = None
+    seen = []
+    for rank in range(world):
+        w, full, gi = bench.build_workload(args, rank, world)
+        assert w.queries[0].tobytes() == full.queries[0].tobytes()
+        for k, s in enumerate(gi):
+            a = w.residues[int(w.offsets[k]):int(w.offsets[k + 1])]
+            b = full.residues[int(full.offsets[s]):int(full.offsets[s + 1])]
+            assert np.array_equal(a, b)
+        seen.append(gi)
+    allidx = np.sort(np.concatenate(seen))
+    assert np.array_equal(allidx, np.arange(full.n_seqs))
+    w1, f1, g1 = bench.build_workload(argparse.Namespace(scaling="weak", n_seqs=3000, n_queries=3), 1, world)
+    assert f1 is None and g1 is None and w1.n_seqs == 3000
