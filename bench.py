@@ -742,6 +742,11 @@ def run_ours(args):
         cpu = {"value": g, "unit": "GCUPS", "cores": threads, "kind": "oracle",
                "sample": f"all {len(w.queries)} queries x the first {info['sequences']} database "
                          f"sequences ({info['residues']} residues), {info['seconds']:.1f} s"}
+        g1, info1 = cpu_oracle_sample(w, max(2.0, args.cpu_seconds / 3), 1)
+        cpu["one_thread"] = {"value": g1, "unit": "GCUPS", "cores": 1,
+                             "sample": f"all {len(w.queries)} queries x the first "
+                                       f"{info1['sequences']} database sequences, "
+                                       f"{info1['seconds']:.1f} s"}
 
     line = {
         "metric": "GCUPS", "value": value, "unit": "GCUPS", "n_gpus": world, "steps": args.steps,
