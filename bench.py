@@ -20,14 +20,20 @@ included). GCUPS = sum(|query|) * sum(|db sequence|) / seconds.
   batched    256 queries against 1,000,000 sequences in one graph-captured batch
              (a persistent launch per rows-per-thread group of query pairs).
   served     the continuous-batching server over 20,000,000 resident sequences,
-             Poisson arrivals: p50 / p99 latency and sustained GCUPS per rate.
+             Poisson arrivals at 10-500 q/s (200 each, bounded queue) and at the
+             0.5-2 q/s knee (64 each): p50 / p99 latency, queueing and service
+             time, sustained and busy GCUPS per rate.
   long_sequences  a 5,478-residue query against 100,000 long sequences (the
-             warp-per-pair kernel) and the same scaled x3 (int32 rescoring).
+             warp-per-pair kernel), the same scaled x3 (int32 rescoring), and with
+             a long tail of 20,000-35,000 residues with and without the block route.
+  traceback  alignments of the top hits of every stream query.
 
+The JSON line ends with compact "batched" and "served" summaries.
 --impl reference times the CPU oracle itself as the reference arm.
-Under torchrun each rank searches its own database shard (weak scaling); the
-JSON line reports the slowest rank's time, and the batched, served, long-sequence
-and traceback legs (single-GPU measurements) are skipped.
+Under torchrun the one database is partitioned over the ranks (strong scaling;
+--scaling weak gives each rank its own database); the JSON line reports the
+slowest rank's time and the merged top-k check, and the batched, served,
+long-sequence and traceback legs (single-GPU measurements) are skipped.
 """
 from __future__ import annotations
 
@@ -84,7 +90,7 @@ def parse_args():
     p.add_argument("--serve-seqs", type=int, default=20_000_000)
     p.add_argument("--serve-rates", default="10,50,100,500",
                    help="comma-separated Poisson arrival rates (queries/s), all past one GPU's "
-                        "capacity of ~2.5 q/s; empty skips them")
+                        "capacity of about 1.8 q/s; empty skips them")
     p.add_argument("--serve-arrivals", type=int, default=200, help="arrivals per overload rate")
     p.add_argument("--serve-knee", default="0.5,1,2",
                    help="arrival rates around one GPU's capacity (the latency knee); empty skips")
