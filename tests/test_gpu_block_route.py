@@ -14,6 +14,7 @@ import pytest
 
 import oracle
 import synth
+from tests import pins
 
 pytestmark = pytest.mark.gpu
 
@@ -102,3 +103,22 @@ def test_long_tail_workload_with_and_without_the_route():
                                     out[0][2].astype(np.int64)]))
     exp = oracle.scores(q, w.residues, w.offsets, w.matrix, w.alpha, w.beta, which=idx)
     assert np.array_equal(out[0][0][idx], exp)
+
+
+def test_block_route_after_save_and_reopen(tmp_path):
+    """A database written by sw_db_save and reopened routes the same sequences (the route
+    is a load option, applied to the reopened sorted order) and scores them exactly."""
+    res, off = _straddling_db(seed=2207, threshold=3000)
+    q = synth.make_queries([900], 2208)[0]
+    exp = oracle.scores(q, res, off, M, 1, 11)
+    path = str(tmp_path / "db.swgb")
+    with sw.sw_db_load(res, off, long_threshold=1000, block_threshold=3000) as db:
+        n_block = db.info()["n_block"]
+        assert n_block > 0
+        sw.sw_db_save(db, path)
+    with sw.sw_db_open(path, block_threshold=3000) as db:
+        assert db.info()["n_block"] == n_block
+        scores, ts, ti, _ = sw.sw_search(db, q, M, 1, 11, 10)
+    assert np.array_equal(scores, exp)
+    ets, eti = pins.ranked_top_k(exp, 10)
+    assert np.array_equal(ts, ets) and np.array_equal(ti, eti)
