@@ -135,8 +135,8 @@ sw_status sw_db_load(const uint8_t* residues, const uint64_t* offsets, uint64_t 
  * residue code below the alphabet or the pad code) and fails with
  * SW_ERR_INVALID_ARG otherwise. The long-sequence threshold is the one the
  * database was loaded with (opts->long_threshold is ignored); device,
- * device_budget and flags come from opts (NULL = defaults). Searches on an
- * opened database give the same results as on the original.
+ * device_budget, flags and block_threshold come from opts (NULL = defaults).
+ * Searches on an opened database give the same results as on the original.
  */
 sw_status sw_db_save(const sw_db* db, const char* path);
 sw_status sw_db_open(const char* path, const sw_db_opts* opts, sw_db** out);
@@ -177,6 +177,12 @@ sw_status sw_search(sw_db* db, const uint8_t* query, uint32_t qlen, const int8_t
  * Codes in d_query are checked on the device: a code >= alphabet makes the
  * result undefined but never an out-of-bounds access (it is clamped to the pad
  * code, which scores 0). Use sw_search for validated input.
+ *
+ * When the database has sequences above its block threshold, their kernel runs
+ * on a stream of the handle, forked from the caller's stream by an event before
+ * the search kernel and joined back into it after: the caller's stream order
+ * holds, and the enqueued work can be captured into a CUDA graph. One handle
+ * serves one such call at a time.
  */
 sw_status sw_search_device(sw_db* db, const uint8_t* d_query, uint32_t qlen,
                            const int8_t* d_matrix, int32_t alpha, int32_t beta, uint32_t top_k,
