@@ -20,7 +20,8 @@ The workloads are the benchmark configurations: the 20-query stream against 2,00
 sequences, a seeded subset of the 256-query batch against 1,000,000 sequences, four
 served queries against the 20,000,000-sequence resident database, and the long-sequence
 workload (5,478-residue query, 100,000 sequences up to 35,000 residues, 1,000 planted
-near-duplicates) with its matrix and penalties scaled by 1 and by 3.
+near-duplicates) with its matrix and penalties scaled by 1 and by 3, and with a tail of 64
+sequences of 20,000-35,000 residues at 100,000 and at 10,000 sequences.
 """
 from __future__ import annotations
 
@@ -72,6 +73,10 @@ def workloads() -> dict:
     return {
         "long_sequences": (lambda: synth.long_sequences(scale=1), [0]),
         "long_sequences_x3": (lambda: synth.long_sequences(scale=3), [0]),
+        # with 64 sequences of 20,000-35,000 residues, at 100,000 and at 10,000 sequences
+        "long_sequences_tail": (lambda: synth.long_sequences(long_tail=64), [0]),
+        "long_sequences_tail_10k": (lambda: synth.long_sequences(n_seqs=10_000, n_planted=100,
+                                                                 long_tail=64), [0]),
         # the four lengths named first are scored first, then the rest
         "query_stream": (synth.query_stream, [0, 9, 14, 19] + [i for i in range(20)
                                                                if i not in (0, 9, 14, 19)]),

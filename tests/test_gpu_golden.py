@@ -11,8 +11,9 @@ the hash and the top-k list. A mismatch names the sixteenths of the vector that 
 Workloads: the 20-query stream against 2,000,000 sequences (each query alone), a seeded
 subset of the 256-query batch against 1,000,000 sequences (all 256 in one graph-captured
 batch), four served queries against the 20,000,000-sequence resident database (plain
-search for the score vectors, the continuous-batching server for the top-k lists), and
-the long-sequence workload scaled by 1 and by 3 (int32 rescoring of the planted pairs).
+search for the score vectors, the continuous-batching server for the top-k lists), the
+long-sequence workload scaled by 1 and by 3 (int32 rescoring of the planted pairs), and
+its long-tail variants at 100,000 and 10,000 sequences with and without the block route.
 """
 import hashlib
 import json
@@ -101,6 +102,24 @@ def test_long_sequences_every_score(name, scale):
         scores, ts, ti, st = sw.sw_search(db, q, w.matrix, w.alpha, w.beta, doc["top_k"])
     assert (st["recomputed"] > 0) == (scale > 1)
     _check_scores(entry, scores, ts, ti, name)
+
+
+@pytest.mark.parametrize("name,n_seqs", [("long_sequences_tail", 100_000),
+                                         ("long_sequences_tail_10k", 10_000)])
+def test_long_tail_every_score_with_and_without_the_block_route(name, n_seqs):
+    """The long-sequence workload with 64 sequences of 20,000-35,000 residues: every score
+    with the block route (the automatic threshold, and one forced low enough to route
+    several hundred sequences) and without it."""
+    doc = _golden(name)
+    w = synth.long_sequences(n_seqs=n_seqs, n_planted=1000 * n_seqs // 100_000, long_tail=64)
+    _check_inputs(doc, w)
+    q = w.queries[0]
+    entry = doc["queries"]["0"]
+    assert _sha(q) == entry["query_sha256"]
+    for bt in (0, 6000, sw.SW_BLOCK_ROUTE_OFF):
+        with sw.sw_db_load(w.residues, w.offsets, long_threshold=3000, block_threshold=bt) as db:
+            scores, ts, ti, _ = sw.sw_search(db, q, w.matrix, w.alpha, w.beta, doc["top_k"])
+        _check_scores(entry, scores, ts, ti, f"{name} block_threshold={bt}")
 
 
 def test_served_stream_every_score_and_served_top_k():
