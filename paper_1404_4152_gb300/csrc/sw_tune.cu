@@ -94,10 +94,14 @@ extern "C" sw_status sw_db_autotune(sw_db* db, const int8_t* matrix, int32_t alp
     bool cached = load_cache(cache_path, key, &t);
     cudaError_t e;
     if (!cached) {
-        // sample: up to 40,000 consecutive sequences of the shorter bin centred on its
-        // residue-weighted median (the lengths that carry most of the work)
+        // sample: consecutive sequences of the shorter bin centred on its residue-weighted
+        // median (the lengths that carry most of the work), as many as make whole rounds of
+        // the persistent grid for every mode (4 rounds of 64-sequence chunks for the modes
+        // that pack two sequences, 8 of 32-sequence chunks for the others): a partial last
+        // round would weigh each mode's timing by a different share of idle SMs
         const uint64_t short_units = (db->n_tiles - db->n_long_tiles) * kTileSeqs;
-        const uint64_t sample = std::min<uint64_t>(short_units, 40000);
+        const uint64_t rounds = (uint64_t)db->grid_short * 2 * wavefront_short_units_per_chunk() * 4;
+        const uint64_t sample = std::min<uint64_t>(short_units, rounds);
         uint64_t centre = db->n_long_tiles;  // tile at the residue median of the short bin
         {
             uint64_t total = 0, acc = 0;
