@@ -521,9 +521,10 @@ def run_served(args, sw, rank):
     del res
     out = []
     runs = [(r, args.serve_arrivals) for r in rates] + [(r, args.serve_knee_arrivals) for r in knee]
-    for ri, (rate, n_arr) in enumerate(runs):
-        out.append(_serve_rate(sw, db, n_res, rate, n_arr, 1407 + ri, args.serve_slots,
-                               args.serve_queue))
+    for rate, n_arr in runs:
+        # each rate's arrival stream and queries depend on the rate alone
+        out.append(_serve_rate(sw, db, n_res, rate, n_arr, 1407 + int(round(rate * 100)),
+                               args.serve_slots, args.serve_queue))
     db.free()
     return {"workload": f"served_stream: {args.serve_seqs:,} resident sequences "
                         f"({n_res / 1e9:.2f} G aa); Poisson arrivals, query lengths log-normal "
