@@ -274,38 +274,59 @@ def check_sharded_top_k(sw, w, full, shard_index, db, d_ts, d_ti, rank, world):
 def batch_padding(qlens, tuning):
     """Padded query rows of a batch under the library's plan rule (queries sorted by length
     and paired, the pair running the longer query's rows for both; each pair on the rows per
-    thread of least measured cost; whole passes of 8 x R rows): computed rows / real rows - 1,
-    and the number of rows-per-thread groups (one persistent launch each)."""
+    thread of least measured cost, whole passes of 8 x R rows; a pair that costs more than
+    its two queries alone in the score-profile ring, and a query without a partner, run
+    there: 24 rows per lane and a short last pass of 8, 16 or 24): computed rows / real
+    rows - 1, the number of rows-per-thread groups (one persistent launch each) and the
+    number of queries run alone (one more launch when any)."""
     Rs = [8, 12, 16, 20, 24]
-    ns = (tuning or {}).get("ns_per_row_residue", {}).get("query_pair") or [0.0] * 5
+    ns_tab = (tuning or {}).get("ns_per_row_residue", {})
+    ns = ns_tab.get("query_pair") or [0.0] * 5
+    ns_ring = ns_tab.get("pair_ring") or [0.0] * 5
+
+    def pass_cost(tab, j, alu):
+        return tab[j] * 8 * Rs[j] if tab[j] > 0 else alu * Rs[j] + 8.0
+
+    def qp_cost(la, j):
+        c = -(-la // (8 * Rs[j])) * pass_cost(ns, j, 3.5)
+        return c * (0.97 if ns[j] <= 0 and Rs[j] == 16 else 1.0)
+
+    def ring_rows(m):  # rows the ring computes for an m-row query, and their cost
+        rem = m % 192
+        last = 0 if rem == 0 else 8 if rem <= 64 else 16 if rem <= 128 else 24
+        cost = (m // 192) * pass_cost(ns_ring, 4, 3.9) + (
+            pass_cost(ns_ring, Rs.index(last), 3.9) if last else 0.0)
+        return (m // 192) * 192 + 8 * last, cost
+
     order = sorted(qlens, reverse=True)
-    computed, groups = 0, set()
+    computed, groups, singles = 0, set(), 0
     for i in range(0, len(order), 2):
         la = order[i]
         lb = order[i + 1] if i + 1 < len(order) else 0
-
-        def cost(j):
-            R = Rs[j]
-            per_pass = ns[j] * 8 * R if ns[j] > 0 else 3.5 * R + 8.0
-            return -(-la // (8 * R)) * per_pass * (0.97 if ns[j] <= 0 and R == 16 else 1.0)
-
-        j = min(range(5), key=cost)
+        j = min(range(5), key=lambda j: qp_cost(la, j))
+        alone = [ring_rows(m) for m in (la, lb) if m]
+        pair = 2 * -(-la // (8 * Rs[j])) * pass_cost(ns, j, 3.5)
+        if lb == 0 or pair > sum(c for _, c in alone):
+            computed += sum(r for r, _ in alone)
+            singles += len(alone)
+            continue
         groups.add(Rs[j])
         computed += 2 * (-(-la // (8 * Rs[j]))) * 8 * Rs[j]
-    return computed / max(1, sum(qlens)) - 1.0, len(groups)
+    return computed / max(1, sum(qlens)) - 1.0, len(groups), singles
 
 
 def run_batched(args, sw, torch, dev, rank):
     """256 queries (lengths uniform in [50, 2000]) vs 1,000,000 sequences in one
     graph-captured batch per step (a persistent launch per rows-per-thread group of query
-    pairs); GCUPS and the kernel-phase time."""
+    pairs, one more for the queries that run alone in the ring); GCUPS and the kernel-phase
+    time."""
     w = synth.query_batch(seed=1406 + 1000 * rank, n_seqs=args.batch_seqs, n_queries=args.batch_queries)
     db = sw.sw_db_load(w.residues, w.offsets, alphabet=20, flags=sw.SW_DB_FLAG_PROFILE)
     tuning = None if args.no_tune else sw.sw_db_autotune(db, w.matrix, w.alpha, w.beta)
     qlens = [int(q.size) for q in w.queries]
     qoff = np.concatenate([[0], np.cumsum(qlens)]).astype(np.uint64)
     nq, n, k = len(qlens), w.n_seqs, w.top_k
-    padded_frac, groups = batch_padding(qlens, tuning)
+    padded_frac, groups, singles = batch_padding(qlens, tuning)
     d_q = torch.from_numpy(np.concatenate(w.queries)).to(dev)
     d_m = torch.from_numpy(w.matrix.copy()).to(dev)
     d_s = torch.empty((nq, n), dtype=torch.int32, device=dev)
@@ -336,7 +357,8 @@ def run_batched(args, sw, torch, dev, rank):
             "value": cells / (ms / 1e3) / 1e9, "unit": "GCUPS", "steps": args.batch_steps,
             "ms_per_step": ms / args.batch_steps, "gpu_launches": int(prof["launches"]),
             "launches_per_batch": int(prof["launches"]) // max(1, args.batch_steps),
-            "wavefront_launches_per_batch": groups, "padded_frac": round(padded_frac, 4)}
+            "wavefront_launches_per_batch": groups + (1 if singles else 0),
+            "queries_alone": singles, "padded_frac": round(padded_frac, 4)}
 
 
 def run_long(args, sw, torch, dev, rank):

@@ -32,6 +32,7 @@ struct BatchGraph {
     std::vector<uint32_t> qlen;
     std::vector<int> group_R;           // the launches: rows per thread and first pair
     std::vector<uint32_t> group_first;
+    std::vector<uint64_t> items;        // the uploaded work items (pairs, then lone queries)
     uint32_t kernels = 0;
 };
 

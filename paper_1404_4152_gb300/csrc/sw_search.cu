@@ -438,6 +438,7 @@ constexpr int kGroupCounter0 = 16;  // the groups' work counters: d_counters[16 
 
 struct BatchPlan {
     std::vector<QueryPair> pairs;
+    std::vector<QueryPair> singles;  // queries that run alone in the ring (len_b = 0)
     std::vector<uint64_t> qoff;
     std::vector<uint32_t> qlen;
     std::vector<int> group_R;
@@ -473,6 +474,28 @@ BatchPlan plan_batch(const sw_db* db, uint32_t nq, const uint64_t* qoffsets) {
             p.len_b = 0;
             p.q_b = 0xffffffffu;
         }
+        // a pair runs its longer query's rows for both halves of the lanes; where that
+        // costs more than the two queries alone in the score-profile ring (one query
+        // against two sequences, 24 rows per lane and a short last pass), or where a
+        // query has no partner, they run alone there
+        const bool ring_ok = !(db->flags & SW_DB_FLAG_QUERY_PROFILE);
+        if (ring_ok && (p.len_b == 0 ||
+                        !pair_pays(db, p.len_a, p.len_b, KernelChoice{KernelChoice::kPairRing, kRingLastR}))) {
+            QueryPair a = p;
+            a.off_b = a.off_a;
+            a.len_b = 0;
+            a.q_b = 0xffffffffu;
+            pl.singles.push_back(a);
+            if (p.len_b) {
+                QueryPair b{};
+                b.off_a = b.off_b = p.off_b;
+                b.len_a = p.len_b;
+                b.q_a = p.q_b;
+                b.q_b = 0xffffffffu;
+                pl.singles.push_back(b);
+            }
+            continue;
+        }
         pl.pairs.push_back(p);
         item_len.push_back(std::max(p.len_a, p.len_b));
     }
@@ -498,7 +521,9 @@ BatchPlan plan_batch(const sw_db* db, uint32_t nq, const uint64_t* qoffsets) {
 
 sw_status upload_plan(sw_db* db, const BatchPlan& pl, cudaStream_t stream) {
     sw_status st;
-    const size_t np = pl.pairs.size(), nq = pl.qlen.size();
+    std::vector<QueryPair> items(pl.pairs);
+    items.insert(items.end(), pl.singles.begin(), pl.singles.end());
+    const size_t np = items.size(), nq = pl.qlen.size();
     if ((st = ensure(db, db->b_pairs, np * sizeof(QueryPair), "batch pairs")) ||
         (st = ensure(db, db->b_qoff, nq * 8, "batch query offsets")) ||
         (st = ensure(db, db->b_qlen, nq * 4, "batch query lengths")) ||
@@ -508,7 +533,7 @@ sw_status upload_plan(sw_db* db, const BatchPlan& pl, cudaStream_t stream) {
         return st;
     cudaError_t e;
     // pageable sources: each copy has consumed its host data when the call returns
-    if ((e = cudaMemcpyAsync(db->b_pairs.p, pl.pairs.data(), np * sizeof(QueryPair),
+    if ((e = cudaMemcpyAsync(db->b_pairs.p, items.data(), np * sizeof(QueryPair),
                              cudaMemcpyHostToDevice, stream)) != cudaSuccess ||
         (e = cudaMemcpyAsync(db->b_qoff.p, pl.qoff.data(), nq * 8, cudaMemcpyHostToDevice,
                              stream)) != cudaSuccess ||
@@ -525,8 +550,9 @@ sw_status launch_batch(sw_db* db, const BatchPlan& pl, const uint8_t* d_queries,
                        cudaStream_t stream) {
     cudaError_t e;
     const uint32_t nq = (uint32_t)pl.qlen.size();
-    static_assert(kGroupCounter0 + kMaxGroups <= kDebugWord, "counter words");
-    if ((e = cudaMemsetAsync(db->d_counters, 0, (kGroupCounter0 + kMaxGroups) * 4, stream)) !=
+    // the query-pair groups' counters, then the ring launch's
+    static_assert(kGroupCounter0 + kMaxGroups + 1 <= kDebugWord, "counter words");
+    if ((e = cudaMemsetAsync(db->d_counters, 0, (kGroupCounter0 + kMaxGroups + 1) * 4, stream)) !=
         cudaSuccess)
         return cuda_fail(e, "batch: counter reset");
     WavefrontArgs a = base_args(db, d_matrix, alpha, beta, d_scores, db->n_seqs, kTileSeqs);
@@ -548,6 +574,19 @@ sw_status launch_batch(sw_db* db, const BatchPlan& pl, const uint8_t* d_queries,
         if ((e = launch_wavefront(kc, a, grid_for(db, kc), stream)) != cudaSuccess)
             return cuda_fail(e, "batch: wavefront kernel");
     }
+    if (!pl.singles.empty()) {  // the queries that run alone: one ring launch
+        const KernelChoice kr{KernelChoice::kPairRing, kRingLastR};
+        WavefrontArgs ar = base_args(db, d_matrix, alpha, beta, d_scores, db->n_seqs,
+                                     units_per_tile(kr));
+        ar.query = d_queries;
+        ar.flag_list = (uint2*)db->b_flags.p;
+        ar.flag_cap = pl.flag_cap;
+        ar.pairs = (const QueryPair*)db->b_pairs.p + pl.pairs.size();
+        ar.n_pairs = (uint32_t)pl.singles.size();
+        ar.work_counter = db->d_counters + kGroupCounter0 + kMaxGroups;
+        if ((e = launch_wavefront(kr, ar, grid_for(db, kr), stream)) != cudaSuccess)
+            return cuda_fail(e, "batch: ring kernel");
+    }
     if ((st = join_block_route(db, forked, stream))) return st;
     RescoreArgs r = rescore_args(db, d_matrix, alpha, beta, d_scores, db->n_seqs);
     r.list = (const uint2*)db->b_flags.p;
@@ -567,6 +606,18 @@ sw_status launch_batch(sw_db* db, const BatchPlan& pl, const uint8_t* d_queries,
     return SW_OK;
 }
 
+// The plan's work items as uploaded: the pairs (grouped), then the queries run alone, each
+// as the 64-bit words of its record (for an exact comparison).
+std::vector<uint64_t> plan_items(const BatchPlan& pl) {
+    std::vector<uint64_t> v;
+    for (const auto* list : {&pl.pairs, &pl.singles})
+        for (const QueryPair& p : *list) {
+            const uint64_t* w = reinterpret_cast<const uint64_t*>(&p);
+            v.insert(v.end(), w, w + sizeof(QueryPair) / 8);
+        }
+    return v;
+}
+
 // Graph replay key: everything a captured batch bakes in.
 bool same_key(const BatchGraph& g, const BatchPlan& pl, const void* q, const void* m,
               int32_t alpha, int32_t beta, uint32_t k, const void* s, const void* ts,
@@ -574,7 +625,7 @@ bool same_key(const BatchGraph& g, const BatchPlan& pl, const void* q, const voi
     return g.exec && g.queries == q && g.matrix == m && g.alpha == alpha && g.beta == beta &&
            g.top_k == k && g.scores == s && g.top_s == ts && g.top_i == ti && g.stream == st &&
            g.qoff == pl.qoff && g.qlen == pl.qlen && g.group_R == pl.group_R &&
-           g.group_first == pl.group_first;
+           g.group_first == pl.group_first && g.items == plan_items(pl);
 }
 
 }  // namespace
@@ -644,8 +695,9 @@ sw_status enqueue_batch(sw_db* db, uint32_t nq, const uint8_t* d_queries,
         g.qlen = pl.qlen;
         g.group_R = pl.group_R;
         g.group_first = pl.group_first;
+        g.items = plan_items(pl);
         g.kernels = (uint32_t)pl.group_R.size() + 1 + (top_k ? topk_launch_count() : 0) +
-                    (db->n_block_tiles ? 1 : 0);
+                    (db->n_block_tiles ? 1 : 0) + (pl.singles.empty() ? 0 : 1);
     }
     PhaseTimer pt(db, 3, stream, pl.cells);
     if ((e = cudaGraphLaunch(g.exec, stream)) != cudaSuccess)
