@@ -631,6 +631,21 @@ __device__ __forceinline__ void ring_passes(const WavefrontArgs& a, const BinArg
                 // block share dup, so the second copy is a branch the whole warp takes or skips
                 auto build = [&](uint32_t at) {
                     if constexpr (kSplit == 1) {
+                        if (A == 20) {  // the protein alphabet: five whole words, no per-code tests
+#pragma unroll
+                            for (int k = 0; k < 5; ++k) {
+                                const uint32_t wa = ma[k * kProfileRows], wb = mb[k * kProfileRows];
+#pragma unroll
+                                for (int b = 0; b < 4; ++b) {
+                                    const uint32_t c = 4u * k + b;
+                                    const uint32_t v = prmt(wa, wb, b | ((8u | b) << 4) |
+                                                                      ((4u + b) << 8) | ((12u + b) << 12));
+                                    if (sw_ok(in_ring(at + c * kCodeBytes), a.dbg, 3))
+                                        sts_u32(at + c * kCodeBytes, v);
+                                }
+                            }
+                            return;
+                        }
 #pragma unroll
                         for (int k = 0; k < 8; ++k) {
                             if (4u * k >= A) break;
