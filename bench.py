@@ -64,12 +64,12 @@ PAPER_PHI_GCUPS_MAX = 58.8    # SWAPHI InterSP, one Xeon Phi 5110P, TrEMBL (Sect
 # per launch: the mean over the 20 launches of one step of the 20-query stream against
 # 2,000,000 sequences, every launch captured (ncu, one pass, full size). Valid for that
 # workload and the kernel source whose sha256 starts with TRAFFIC_SOURCE.
-TRAFFIC_BYTES_PER_LAUNCH = 18.81e9
-TRAFFIC_SOURCE = "a61900cdfdd889e2"
+TRAFFIC_BYTES_PER_LAUNCH = 18.60e9
+TRAFFIC_SOURCE = "6984e149683534ad"
 # ALU-pipe work per row update of that kernel (sm__pipe_alu_cycles_active over row updates,
-# 8.12 cycles, in two-cycle instruction equivalents; an 807-residue query's launch): the mix
+# 7.83 cycles, in two-cycle instruction equivalents; an 807-residue query's launch): the mix
 # the kernel executes, against the 3.5 minimum
-ALU_OPS_PER_CELL_MEASURED = 4.06
+ALU_OPS_PER_CELL_MEASURED = 3.92
 
 
 def parse_args():
