@@ -18,7 +18,10 @@ included). GCUPS = sum(|query|) * sum(|db sequence|) / seconds.
              ALU-pipe peak at the SM clock sampled during the run.
   cpu_baseline  the CPU oracle on a bounded sample of the same workload.
   batched    256 queries against 1,000,000 sequences in one graph-captured batch
-             (a persistent launch per rows-per-thread group of query pairs).
+             (a persistent launch per rows-per-thread group of query pairs, one more
+             for the queries that run alone), against the config-1 loop (vs_plain)
+             and against the same queries one at a time on the same database, with
+             every score compared (vs_loop_same_db).
   served     the continuous-batching server over 20,000,000 resident sequences,
              Poisson arrivals at 10-500 q/s (200 each, bounded queue) and at the
              0.5-2 q/s knee (64 each): p50 / p99 latency, queueing and service
@@ -85,6 +88,8 @@ def parse_args():
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--batch-steps", type=int, default=1,
                    help="timed steps of the batched workload (0 skips it)")
+    p.add_argument("--batch-loop", action=argparse.BooleanOptionalAction, default=True,
+                   help="also time the batch's queries one at a time on the same database")
     p.add_argument("--batch-seqs", type=int, default=1_000_000)
     p.add_argument("--batch-queries", type=int, default=256)
     p.add_argument("--serve-seqs", type=int, default=20_000_000)
@@ -235,6 +240,8 @@ def compact_batched(b):
     if not b:
         return None
     return {"gcups": round(b["value"], 1), "vs_plain": round(b.get("vs_plain", 0.0), 4),
+            "vs_loop_same_db": (round(b["vs_loop_same_db"], 4) if b.get("vs_loop_same_db")
+                                else None),
             "padded_frac": b.get("padded_frac"), "launches_per_batch": b.get("launches_per_batch"),
             "ms_per_step": round(b["ms_per_step"], 1)}
 
@@ -350,6 +357,21 @@ def run_batched(args, sw, torch, dev, rank):
     ms = e0.elapsed_time(e1)
     prof = sw.sw_db_get_profile(db)
     cells = sum(qlens) * w.db_residues * args.batch_steps
+    loop = None
+    if args.batch_loop:
+        # the same queries one at a time on the same database and buffers (one pass), and
+        # whether every score equals the batch's
+        batch_scores = d_s.clone()
+        e0.record(stream)
+        for i in range(nq):
+            sw.sw_search_device(db, d_q[int(qoff[i]):int(qoff[i + 1])], qlens[i], d_m, w.alpha,
+                                w.beta, k, d_s[i], d_ts[i], d_ti[i], stream)
+        e1.record(stream)
+        stream.synchronize()
+        lms = e0.elapsed_time(e1)
+        loop = {"gcups": sum(qlens) * w.db_residues / (lms / 1e3) / 1e9, "ms": lms,
+                "scores_identical": bool(torch.equal(batch_scores, d_s))}
+        del batch_scores
     db.free()
     return {"workload": f"query_batch: {nq} queries, lengths uniform [50, 2000] (sum {sum(qlens)}), "
                         f"vs {n:,} sequences ({w.db_residues / 1e6:.0f} M aa), one graph-captured "
@@ -358,7 +380,9 @@ def run_batched(args, sw, torch, dev, rank):
             "ms_per_step": ms / args.batch_steps, "gpu_launches": int(prof["launches"]),
             "launches_per_batch": int(prof["launches"]) // max(1, args.batch_steps),
             "wavefront_launches_per_batch": groups + (1 if singles else 0),
-            "queries_alone": singles, "padded_frac": round(padded_frac, 4)}
+            "queries_alone": singles, "padded_frac": round(padded_frac, 4),
+            "loop_same_db": loop,
+            "vs_loop_same_db": (cells / (ms / 1e3) / 1e9) / loop["gcups"] if loop else None}
 
 
 def run_long(args, sw, torch, dev, rank):
