@@ -725,41 +725,24 @@ __device__ __forceinline__ void ring_passes(const WavefrontArgs& a, const BinArg
                     e_cur = e_nxt;
                 }
                 const uint32_t koff = S == 1 ? k * kSlot : (k & 1) * Geo::kPlane + (k >> 1) * kSlot;
+                // x = H[i-1][j-1] + fsbt of every row first (last row first, in place: the
+                // row below has used the old H by then), then the H, E, F chain down the rows
+#pragma unroll
+                for (int r = RR - 1; r >= 0; --r) {
+                    V sc = 0;
+                    if (sw_ok(in_ring(cur[r] + koff), a.dbg, 2)) sc = lds_u32(cur[r] + koff);
+                    Hl[r] = Lane::vadd(r > 0 ? Hl[r - 1] : hdiag0, sc);
+                }
                 V E = e_in;
-                if constexpr (T == kShortT && RR == kRingLastR) {
-                    // down the rows: x = H[i-1][j-1] + fsbt, then H, E and F
-                    V diag = hdiag0;
 #pragma unroll
-                    for (int r = 0; r < RR; ++r) {
-                        V sc = 0;
-                        if (sw_ok(in_ring(cur[r] + koff), a.dbg, 2)) sc = lds_u32(cur[r] + koff);
-                        const V x = Lane::vadd(diag, sc);          // H[i-1][j-1] + fsbt
-                        const V H = Lane::max3_relu(x, E, Fr[r]);  // H[i][j]
-                        diag = Hl[r];                              // H[i][j-1]: diagonal of row i+1
-                        Hl[r] = H;
-                        const V hb = Lane::vadd(H, vbeta);         // H[i][j] - beta
-                        E = Lane::addmax(E, valpha, hb);           // E[i+1][j]
-                        Fr[r] = Lane::addmax(Fr[r], valpha, hb);   // F[i][j+1]
-                        best = Lane::vmax(best, x);                // max H = max(0, max x)
-                    }
-                } else {
-                    // x of every row first (last row first, in place), then the chain
-#pragma unroll
-                    for (int r = RR - 1; r >= 0; --r) {
-                        V sc = 0;
-                        if (sw_ok(in_ring(cur[r] + koff), a.dbg, 2)) sc = lds_u32(cur[r] + koff);
-                        Hl[r] = Lane::vadd(r > 0 ? Hl[r - 1] : hdiag0, sc);
-                    }
-#pragma unroll
-                    for (int r = 0; r < RR; ++r) {
-                        const V x = Hl[r];
-                        const V H = Lane::max3_relu(x, E, Fr[r]);  // H[i][j]
-                        Hl[r] = H;
-                        const V hb = Lane::vadd(H, vbeta);         // H[i][j] - beta
-                        E = Lane::addmax(E, valpha, hb);           // E[i+1][j]
-                        Fr[r] = Lane::addmax(Fr[r], valpha, hb);   // F[i][j+1]
-                        best = Lane::vmax(best, x);                // max H = max(0, max x)
-                    }
+                for (int r = 0; r < RR; ++r) {
+                    const V x = Hl[r];
+                    const V H = Lane::max3_relu(x, E, Fr[r]);      // H[i][j]
+                    Hl[r] = H;
+                    const V hb = Lane::vadd(H, vbeta);             // H[i][j] - beta
+                    E = Lane::addmax(E, valpha, hb);               // E[i+1][j]
+                    Fr[r] = Lane::addmax(Fr[r], valpha, hb);       // F[i][j+1]
+                    best = Lane::vmax(best, x);                    // max H = max(0, max x)
                 }
                 hb_out = Hl[RR - 1];
                 eb_out = E;
